@@ -1,0 +1,220 @@
+"""Checks that pin the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each check takes an ``oracle.Oracle`` instance so the same checks can run
+against deliberately broken copies of the oracle (tests/test_oracle_mutants.py)
+and prove that they catch plausible mistakes.  None of these checks reuses the
+oracle's own code path as its expected value:
+
+* counts: an independent numpy ``bincount`` of the cell index (Sec. III,
+  Fig. 1), brute force over every triplet of tiny inputs;
+* K2: exact big-integer factorials, exp(K2) = prod (r+1)! / (r0! r1!) (Eq. 1),
+  and hand-worked tables (tests/golden/k2_hand.json);
+* log-factorials: math.lgamma;
+* ranking: numpy lexsort over every triplet, exact FP64 ties from duplicated
+  SNP columns, and recovery of a strongly planted triplet (lowest K2 wins,
+  Sec. III).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+
+import gen
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def tiny_data(m, n, n_cases, seed, maf=(0.05, 0.5)):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(maf[0], maf[1], size=m)
+    g = rng.binomial(2, p[:, None], size=(m, n)).astype(np.uint8)
+    ph = np.zeros(n, dtype=np.uint8)
+    ph[rng.choice(n, size=n_cases, replace=False)] = 1
+    return g, ph
+
+
+def all_triplets(m):
+    return np.array(list(itertools.combinations(range(m), 3)), dtype=np.int32).reshape(-1, 3)
+
+
+def numpy_tables(g, ph, trip):
+    """Independent counting: bincount of class*27 + 9 gX + 3 gY + gZ."""
+    out = np.empty((len(trip), 2, 27), dtype=np.int64)
+    for t, (x, y, z) in enumerate(trip):
+        idx = ph.astype(np.int64) * 27 + 9 * g[x].astype(np.int64) + 3 * g[y] + g[z]
+        out[t] = np.bincount(idx, minlength=54).reshape(2, 27)
+    return out
+
+
+def exact_k2(table):
+    """log of prod_cells (r+1)! / (r0! r1!), an integer, with Python big ints."""
+    num = 1
+    for c in range(27):
+        r0, r1 = int(table[0][c]), int(table[1][c])
+        num *= math.factorial(r0 + r1 + 1) // (math.factorial(r0) * math.factorial(r1))
+    return math.log(num)
+
+
+def check_lf(o):
+    lf = o.log_factorials(30000)
+    assert lf[0] == 0.0 and lf[1] == 0.0
+    n = np.array([2, 3, 10, 100, 1000, 5000, 16385, 20001, 30000])
+    ref = np.array([math.lgamma(float(v) + 1.0) for v in n])
+    assert np.allclose(lf[n], ref, rtol=1e-12, atol=0), (lf[n], ref)
+
+
+def check_hand_values(o):
+    with open(os.path.join(GOLDEN, "k2_hand.json")) as f:
+        cases = json.load(f)["cases"]
+    tabs = np.zeros((len(cases), 2, 27), dtype=np.int32)
+    for t, c in enumerate(cases):
+        for cell, (r0, r1) in c["cells"].items():
+            tabs[t, 0, int(cell)] = r0
+            tabs[t, 1, int(cell)] = r1
+    got = o.k2(tabs)
+    want = np.array([c["k2"] for c in cases])
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-15), (got, want)
+
+
+def check_k2_bigint(o, seed=3):
+    rng = np.random.default_rng(seed)
+    tabs = []
+    for scale in (1, 3, 30, 300, 3000):
+        for _ in range(6):
+            t = rng.integers(0, scale + 1, size=(2, 27))
+            t[:, rng.random(27) < 0.3] = 0          # some empty cells
+            tabs.append(t)
+    tabs.append(np.zeros((2, 27), dtype=np.int64))
+    one = np.zeros((2, 27), dtype=np.int64)
+    one[1, 26] = 20000                                 # one pure cell, large N
+    tabs.append(one)
+    tabs = np.array(tabs, dtype=np.int32)
+    got = o.k2(tabs)
+    want = np.array([exact_k2(t) for t in tabs])
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12), np.max(np.abs(got - want))
+
+
+def check_tables_bruteforce(o):
+    for (m, n, n1, seed) in [(5, 1, 0, 1), (6, 33, 10, 2), (9, 64, 40, 3), (12, 100, 37, 4),
+                             (7, 65, 65, 5), (8, 97, 0, 6)]:
+        g, ph = tiny_data(m, n, n1, seed)
+        trip = all_triplets(m)
+        got = o.tables(g, ph, trip)
+        assert np.array_equal(got, numpy_tables(g, ph, trip)), (m, n)
+        # SNPs given out of order: X, Y, Z take the listed roles
+        perm = trip[:, [2, 0, 1]]
+        assert np.array_equal(o.tables(g, ph, perm), numpy_tables(g, ph, perm))
+
+
+def check_invariants(o, seed=11):
+    g, ph = tiny_data(10, 90, 41, seed)
+    trip = all_triplets(10)
+    tab = o.tables(g, ph, trip).astype(np.int64)          # [t, 2, 27]
+    n1 = int(ph.sum())
+    assert np.all(tab[:, 0].sum(1) == 90 - n1) and np.all(tab[:, 1].sum(1) == n1)
+    cube = tab.reshape(-1, 2, 3, 3, 3)                    # [t, c, gX, gY, gZ]
+
+    def pair_table(a, b):
+        idx = ph.astype(np.int64) * 9 + 3 * g[a].astype(np.int64) + g[b]
+        return np.bincount(idx, minlength=18).reshape(2, 3, 3)
+
+    for t, (x, y, z) in enumerate(trip):
+        assert np.array_equal(cube[t].sum(3), pair_table(x, y))
+        assert np.array_equal(cube[t].sum(2), pair_table(x, z))
+        assert np.array_equal(cube[t].sum(1), pair_table(y, z))
+        single = np.bincount(ph.astype(np.int64) * 3 + g[x], minlength=6).reshape(2, 3)
+        assert np.array_equal(cube[t].sum((2, 3)), single)
+
+
+def check_symmetries(o, seed=12):
+    g, ph = tiny_data(9, 120, 50, seed)
+    trip = all_triplets(9)
+    base = o.scores(g, ph, trip)
+    ref = np.array([exact_k2(t) for t in numpy_tables(g, ph, trip)])
+    assert np.allclose(base, ref, rtol=1e-13)
+    for perm in itertools.permutations(range(3)):
+        assert np.allclose(o.scores(g, ph, trip[:, list(perm)]), base, rtol=1e-12)
+    g2 = g.copy()
+    g2[4] = 2 - g2[4]                                     # relabel 0 <-> 2 at one SNP
+    assert np.allclose(o.scores(g2, ph, trip), base, rtol=1e-12)
+    assert np.allclose(o.scores(g, 1 - ph, trip), base, rtol=1e-12)   # swap classes
+
+
+def check_monomorphic(o, seed=13):
+    g, ph = tiny_data(6, 77, 30, seed)
+    g[5] = 0                                              # SNP 5 monomorphic
+    trip = np.array([[0, 1, 5], [2, 3, 5], [1, 4, 5]], dtype=np.int32)
+    got = o.scores(g, ph, trip)
+    for t, (x, y, _) in enumerate(trip):
+        idx = ph.astype(np.int64) * 9 + 3 * g[x].astype(np.int64) + g[y]
+        pt = np.bincount(idx, minlength=18).reshape(2, 9)
+        num = 1
+        for c in range(9):
+            r0, r1 = int(pt[0, c]), int(pt[1, c])
+            num *= math.factorial(r0 + r1 + 1) // (math.factorial(r0) * math.factorial(r1))
+        assert math.isclose(got[t], math.log(num), rel_tol=1e-13)
+
+
+def check_degenerate(o):
+    # a single class: every term is log(r + 1)
+    for n1 in (0, 40):
+        g, ph = tiny_data(5, 40, n1, 21)
+        trip = all_triplets(5)
+        tab = numpy_tables(g, ph, trip)
+        want = np.array([sum(math.log(int(t[0, c] + t[1, c]) + 1) for c in range(27)) for t in tab])
+        assert np.allclose(o.scores(g, ph, trip), want, rtol=1e-13)
+    # M = 3: the scan returns the only triplet with its score
+    g, ph = tiny_data(3, 50, 20, 22)
+    tr, sc, _ = o.scan_topk(g, ph, 1)
+    assert tr.tolist() == [[0, 1, 2]]
+    assert math.isclose(sc[0], exact_k2(numpy_tables(g, ph, [[0, 1, 2]])[0]), rel_tol=1e-13)
+    # one sample
+    g, ph = tiny_data(4, 1, 1, 23)
+    assert np.allclose(o.scores(g, ph, all_triplets(4)), math.log(2.0), rtol=1e-15)
+
+
+def check_scan_bruteforce(o):
+    for (m, n, n1, seed, k) in [(11, 70, 30, 31, 7), (14, 129, 64, 32, 20), (9, 31, 31, 33, 84)]:
+        g, ph = tiny_data(m, n, n1, seed)
+        trip = all_triplets(m)
+        s = np.array([exact_k2(t) for t in numpy_tables(g, ph, trip)])
+        s_oracle = o.scores(g, ph, trip)
+        assert np.allclose(s_oracle, s, rtol=1e-13)
+        order = np.lexsort((trip[:, 2], trip[:, 1], trip[:, 0], s_oracle))
+        tr, sc, _ = o.scan_topk(g, ph, k)
+        assert np.array_equal(tr, trip[order[:k]])
+        assert np.array_equal(sc, s_oracle[order[:k]])
+        assert np.all(np.diff(sc) >= 0)
+
+
+def check_ties(o):
+    # duplicated columns give bit-identical tables, hence exactly equal K2;
+    # equal K2 is ordered by (i, j, k).
+    d = gen.make_dataset(30, 600, 300, (0.3, 0.5), 1, seed=5, odds_ratio=10.0)
+    g = d.genotypes.copy()
+    i, j, k = d.planted[0]
+    free = [c for c in range(30) if c not in (i, j, k)]
+    dup = free[-1]
+    g[dup] = g[k]
+    tr, sc, _ = o.scan_topk(g, d.phenotype, 4)
+    want = sorted([tuple(sorted((i, j, k))), tuple(sorted((i, j, dup)))])
+    assert [tuple(t) for t in tr[:2]] == want
+    assert sc[0] == sc[1]
+    assert sc[2] > sc[1]
+
+
+def check_planted_recovery(o):
+    # A strongly planted interaction scores lowest (Sec. III: lowest K2 wins).
+    for seed in range(1, 6):
+        d = gen.make_dataset(40, 800, 400, (0.3, 0.5), 1, seed=seed, odds_ratio=10.0)
+        tr, sc, _ = o.scan_topk(d.genotypes, d.phenotype, 3)
+        assert tuple(tr[0]) == d.planted[0], (seed, tr[0], d.planted[0])
+
+
+ALL_CHECKS = [check_lf, check_hand_values, check_k2_bigint, check_tables_bruteforce,
+              check_invariants, check_symmetries, check_monomorphic, check_degenerate,
+              check_scan_bruteforce, check_ties, check_planted_recovery]

@@ -1,0 +1,40 @@
+"""The oracle's pins have teeth: each plausible mistake, planted in a copy of
+the oracle's C source on the CPU, fails at least one pin."""
+import os
+
+import pytest
+
+import oracle
+import oracle_pins as pins
+
+MUTANTS = {
+    "cell_index_transposed": ("9 * a + 3 * b + d", "3 * a + 9 * b + d"),
+    "dropped_plus_one": ("lf[r0 + r1 + 1] - lf[r0]", "lf[r0 + r1] - lf[r0]"),
+    "wrong_sign": (") - lf[r1];", ") + lf[r1];"),
+    "dropped_term": ("(lf[r0 + r1 + 1] - lf[r0]) - lf[r1]", "lf[r0 + r1 + 1] - lf[r0]"),
+    "classes_swapped": ("ft[c * NCELL + 9", "ft[(1 - c) * NCELL + 9"),
+    "log_shifted": ("log((double)n)", "log((double)(n + 1))"),
+    "highest_wins": ("return a->k2 < b->k2;", "return a->k2 > b->k2;"),
+    "tiebreak_reversed": ("return a->i < b->i;", "return a->i > b->i;"),
+    "last_sample_dropped": ("s < n_samples; ++s", "s + 1 < n_samples; ++s"),
+    "k_loop_skips": ("int32_t k = j + 1;", "int32_t k = j + 2;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    before, after = MUTANTS[name]
+    with open(oracle._SRC) as f:
+        src = f.read()
+    assert before in src, f"mutation site for {name} not found"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(before, after, 1))
+    lib = oracle.build(force=True, src=str(path), out=str(tmp_path / f"lib{name}.so"))
+    o = oracle.Oracle(lib)
+    caught = []
+    for check in pins.ALL_CHECKS:
+        try:
+            check(o)
+        except (AssertionError, ValueError):
+            caught.append(check.__name__)
+    assert caught, f"no pin catches the {name} mutant"
