@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput of the exhaustive three-way epistasis scan on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config large] [--impl ours|reference]
+
+One step = one whole scan (count every triplet's 2 x 27 table, FP32 K2, candidate
+selection, FP64 rescoring, top-k) of the workload, with the packed data resident on
+the GPU.  Metric: tera sample-triplets per second, C(M,3) * N / step time (the
+paper's "combinations x samples / s", Sec. V).  Prints one JSON line on rank 0.
+
+N > 1 (torchrun): the SNP-pair range is split into N slices of equal triplet count,
+each rank scans its slice on its own GPU, and rank 0 merges the per-slice top-k by
+(K2, i, j, k).  --impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+WORKLOADS = {
+    "tiny": "64 SNPs x 512 samples (256 cases), MAF U[0.05,0.5], 1 planted triplet, top-10",
+    "medium": "1024 SNPs x 8192 samples (4096 cases), MAF U[0.05,0.5], 2 planted triplets, top-10",
+    "large": "2048 SNPs x 16384 samples (6554 cases), MAF U[0.01,0.5], 1 planted triplet, top-10",
+    "stress": "4096 SNPs x 4096 samples (2048 cases), MAF U[0.02,0.5], 4 planted triplets "
+              "+ 2 duplicated columns, top-64",
+}
+METRIC = "tera sample-triplets/s (K2 scored)"
+UNIT = "Tsample-triplets/s"
+POPC_PER_SM_CLK = 16          # 32-bit POPC issue rate per SM per clock (measured, see DESIGN)
+L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
+# DRAM bytes per launch of the dominant kernel from one ncu capture (None until captured
+# for the current kernel), keyed by (path, workload).
+TRAFFIC = {}
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def shard_pairs(m, world, rank):
+    """Pair range [a, b) of this rank: equal triplet counts (pair p = j(j-1)/2 + i has
+    M-1-j triplets)."""
+    j = np.arange(1, m, dtype=np.int64)
+    per_pair_j = (m - 1 - j)                    # triplets per pair with this j
+    pairs_j = j                                 # pairs with this j
+    cum = np.concatenate([[0], np.cumsum(per_pair_j * pairs_j)])
+    total = int(cum[-1])
+    lo_t, hi_t = total * rank // world, total * (rank + 1) // world
+
+    def pair_at(t):  # first pair index whose cumulative triplets reach t
+        if t >= total:
+            return m * (m - 1) // 2
+        q = int(np.searchsorted(cum, t, side="right")) - 1  # j-block
+        jj = q + 1
+        start = jj * (jj - 1) // 2
+        w = m - 1 - jj
+        return start + ((t - int(cum[q])) // w if w > 0 else 0)
+
+    return pair_at(lo_t), pair_at(hi_t)
+
+
+def merge_topk(rows, k):
+    rows = sorted(rows)
+    return rows[:k]
+
+
+def cpu_baseline(d, budget_s=15.0, seed=0):
+    """The oracle as it stands, timed on the host cores on a bounded random sample
+    of the workload's triplets (rate in tera sample-triplets/s)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    probe = gen.random_triplets(d.n_snps, 256, seed=seed)
+    t0 = time.perf_counter()
+    oracle.scores(d.genotypes, d.phenotype, probe, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    n = int(max(256, min(50_000_000, 256 * budget_s / dt)))
+    samp = gen.random_triplets(d.n_snps, n, seed=seed + 1)
+    t0 = time.perf_counter()
+    oracle.scores(d.genotypes, d.phenotype, samp, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n * d.n_samples / dt / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} uniformly random triplets of the {d.n_snps}x{d.n_samples} workload, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    d = gen.make_config(args.config, seed=args.seed)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(d, budget_s=min(per_step, 5.0))
+    vals = []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        vals.append(cpu_baseline(d, budget_s=per_step, seed=100 + s))
+    wall = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"] + " (per step)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2201_10956_gb300 as epi
+    from paper_2201_10956_gb300 import build as B
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    B.build()
+    d = gen.make_config(args.config, seed=args.seed)
+    m, n, k = d.n_snps, d.n_samples, d.top_k
+    pb, pe = shard_pairs(m, world, rank)
+    stream = torch.cuda.Stream()
+    g_dev = torch.from_numpy(d.genotypes).cuda()
+    p_dev = torch.from_numpy(d.phenotype).cuda()
+    torch.cuda.synchronize()
+    h = epi.Handle(g_dev, p_dev, stream=stream)
+    h.set_option("path", args.path)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        if world == 1:
+            return h.scan(k)
+        return h.scan_range(pb, pe, k)
+
+    for _ in range(args.warmup):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms, sel_ms = [], []
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = None
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s)                  # L2 flush, outside the step's events
+            ev[s][0].record(stream)
+        out = step()
+        with torch.cuda.stream(stream):
+            ev[s][1].record(stream)
+        st = h.stats()
+        kern_ms.append(st["scan_kernel_ms"])
+        sel_ms.append(st["select_ms"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    mine = sum(step_ms) / 1000.0
+    t = torch.tensor([mine], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    units = gen.n_triplets(m) * n  # sample-triplets per step, all ranks together
+    value = units * args.steps / t_max / 1e12
+    # top-k of the whole scan (rank 0 merges the slices)
+    trip, sc = out
+    trip = trip.cpu().numpy() if hasattr(trip, "cpu") else trip
+    sc = sc.cpu().numpy() if hasattr(sc, "cpu") else sc
+    rows = [(float(a), *map(int, b)) for a, b in zip(sc, trip)]
+    if dist:
+        allrows = [None] * world
+        dist.all_gather_object(allrows, rows)
+        rows = merge_topk([r for part in allrows for r in part], k)
+    st = h.stats()
+    h.close()
+    if rank != 0:
+        return
+
+    # end to end through the public API with host buffers: H2D of the genotypes, pack,
+    # scan, D2H of the top-k, every step (1 GPU).
+    e2e = None
+    if not args.no_e2e and world == 1:
+        g_pin = torch.from_numpy(d.genotypes).pin_memory()
+        p_pin = torch.from_numpy(d.phenotype).pin_memory()
+        e_steps = max(1, min(args.steps, 3))
+        h2 = epi.Handle(g_pin.numpy(), p_pin.numpy())
+        h2.set_option("path", args.path)
+        h2.scan(k)
+        h2.close()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(e_steps):
+            h2 = epi.Handle(g_pin.numpy(), p_pin.numpy())
+            h2.set_option("path", args.path)
+            h2.scan(k)
+            h2.close()
+        torch.cuda.synchronize()
+        e_dt = (time.perf_counter() - t1) / e_steps
+        e2e = {"value": units / e_dt / 1e12, "unit": UNIT, "h2d_bytes_per_step": m * n + n,
+               "d2h_bytes_per_step": k * (3 * 4 + 8) + 64, "steps": e_steps,
+               "ms_per_step": 1000 * e_dt}
+
+    props = torch.cuda.get_device_properties(local_rank)
+    peaks = read_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    kern_s = statistics.mean(kern_ms) / 1000.0
+    popc_alg = gen.n_triplets(m) * n * 27.0 / 32.0     # 32-bit POPC per launch (27-cell form)
+    if world > 1:
+        popc_alg /= world
+    peak_popc = props.multi_processor_count * sm_max * 1e6 * POPC_PER_SM_CLK
+    achieved = popc_alg / kern_s
+    traffic = TRAFFIC.get((args.path, args.config))
+    roofline = {"bound": "alu", "kernel": "scan_popc27_kernel", "achieved": achieved / 1e12,
+                "peak": peak_popc / 1e12, "unit": "TPOPC/s", "frac": achieved / peak_popc,
+                "traffic": traffic,
+                "peak_note": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
+                             f"{POPC_PER_SM_CLK} POPC/SM/clk",
+                "kernel_ms": 1000 * kern_s, "select_ms": statistics.mean(sel_ms)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "path": args.path,
+                       "top_k": k, "l2": "flushed before every timed step (512 MB write)",
+                       "wall_s": wall},
+            "gpu_launches": st["kernel_launches"] * args.steps,
+            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "top": [list(r[1:]) for r in rows[:3]]}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(d, budget_s=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--path", default="popc")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

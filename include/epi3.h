@@ -1,0 +1,169 @@
+/*
+ * epi3 -- exhaustive three-way epistasis scan on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library.  The method is the one of arXiv 2201.10956
+ * ("Unlocking Personalized Healthcare on Modern CPUs/GPUs: Three-way Gene
+ * Interaction Study"):
+ *
+ *   - Sec. III: a case-control data set of M SNPs x N samples.  Genotype
+ *     values are 0 (homozygous major), 1 (heterozygous), 2 (homozygous minor);
+ *     the phenotype is 0 (control) or 1 (case).
+ *   - Sec. III / Fig. 1: for a SNP triplet (X, Y, Z) the frequency table holds,
+ *     for each genotype combination (gX, gY, gZ) in {0,1,2}^3 and each class,
+ *     the number of samples showing it.  Here: table[c][cell], c = 0 controls,
+ *     c = 1 cases, cell = 9 gX + 3 gY + gZ, X < Y < Z the SNP indices.
+ *   - Eq. 1: the Bayesian K2 score of a table, natural log:
+ *       K2 = sum_cells [ log((r+1)!) - log(r0!) - log(r1!) ],  r = r0 + r1.
+ *   - Sec. III: the solution is the triplet of lowest K2.  The library returns
+ *     the top_k lowest under the total order (K2, i, j, k) ascending, so exact
+ *     ties are broken by the SNP indices.
+ *
+ * Every function returns EPI3_OK (0) or a negative EPI3_ERR_* code, and sets a
+ * thread-local message readable with epi3_last_error().  Nothing falls back to
+ * the CPU: without a usable sm_103 device calls fail with EPI3_ERR_UNSUPPORTED.
+ */
+#ifndef EPI3_H
+#define EPI3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPI3_VERSION 1
+
+/* status codes */
+#define EPI3_OK 0
+#define EPI3_ERR_ARG (-1)         /* bad pointer, size, genotype > 2, phenotype > 1, top_k */
+#define EPI3_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define EPI3_ERR_OOM (-3)         /* device or pinned host allocation failed */
+#define EPI3_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out */
+#define EPI3_ERR_UNSUPPORTED (-5) /* no sm_103 device, or a path/size this build lacks */
+#define EPI3_ERR_OVERFLOW (-6)    /* more near-tied candidates than the candidate stage holds */
+
+/* epi3_create flags */
+#define EPI3_DEVICE_PTRS 1 /* genotypes/phenotype (and scan outputs) are device pointers */
+
+/* counting paths (epi3_tables, option "path") */
+#define EPI3_PATH_AUTO 0
+#define EPI3_PATH_POPC 1 /* 27-cell LOP3 AND + POPC over bit planes (Alg. 2 counting) */
+
+#define EPI3_MAX_TOPK 512
+
+typedef struct epi3_handle epi3_handle;
+
+/*
+ * Create a handle: split the samples by class, pack genotypes into bit planes
+ * on the device (one plane for genotype 0, one for genotype 1, per class; the
+ * genotype-2 plane is never stored and is derived by NOR, Sec. IV-A), and
+ * build the log-factorial tables of Eq. 1.
+ *
+ *   genotypes   [n_snps][n_samples] uint8, values 0..2, SNP-major, row stride
+ *               n_samples (Sec. III data set D with SNPs as rows).
+ *   phenotype   [n_samples] uint8, 0 = control, 1 = case.
+ *   n_snps      M >= 3.   n_samples  N >= 1 (at most 131072).
+ *   flags       0: genotypes/phenotype are host memory, copied during the call;
+ *               EPI3_DEVICE_PTRS: they are device memory on the current device,
+ *               read by the pack kernels during the call.
+ *   cuda_stream a cudaStream_t the handle issues all its work on, or NULL for a
+ *               stream the library creates and owns.
+ *
+ * The caller keeps ownership of all inputs; the handle keeps only the packed
+ * planes.  On error *h is set to NULL.  Values out of range give EPI3_ERR_ARG.
+ */
+int epi3_create(epi3_handle** h, const uint8_t* genotypes, const uint8_t* phenotype,
+                int32_t n_snps, int32_t n_samples, int32_t flags, void* cuda_stream);
+
+/*
+ * Exhaustive scan over every triplet i < j < k (Sec. III, Alg. 2): count the
+ * 2 x 27 table, score it with K2 (Eq. 1) and keep the top_k lowest.
+ *
+ *   top_k         1..min(EPI3_MAX_TOPK, C(M,3))  (EPI3_MAX_TOPK = 512).
+ *   out_triplets  [top_k][3] int32, (i, j, k) with i < j < k, 0-based.
+ *   out_scores    [top_k] double, K2 ascending.
+ *
+ * Tables are counted exactly (int32).  Every triplet is scored in FP32 from a
+ * split log-factorial table; the candidates that can decide the answer (FP32
+ * score within the proven FP32 error band of the k-th best) are recounted and
+ * rescored in FP64, and the answer is ordered by (FP64 K2, i, j, k).  The
+ * returned scores are those FP64 values.  Outputs are host memory unless the
+ * handle was created with EPI3_DEVICE_PTRS.  The call returns when the results
+ * are written.  EPI3_ERR_OVERFLOW means that more than 8192 triplets tie within
+ * the FP32 error band of the k-th best score.
+ */
+int epi3_scan(epi3_handle* h, int32_t top_k, int32_t* out_triplets, double* out_scores);
+
+/*
+ * The scan restricted to the SNP pairs (i, j) whose index in the order
+ * (j ascending, then i ascending) lies in [pair_begin, pair_end): all triplets
+ * (i, j, k) with k > j of those pairs.  Pair p = j (j - 1) / 2 + i.  Slices
+ * that cover [0, C(M,2)) once give, merged by (K2, i, j, k), the full scan's
+ * answer, so a scan can be split, resumed or spread over devices.  Outputs as
+ * epi3_scan; top_k is clipped to the slice's triplet count and the number of
+ * rows written is returned through *n_out.
+ */
+int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_t top_k,
+                    int32_t* out_triplets, double* out_scores, int32_t* n_out);
+
+/* Release the handle's device memory, stream (if owned) and events. */
+int epi3_destroy(epi3_handle* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* epi3_last_error(void);
+
+/*
+ * Debug / test: the exact 2 x 27 tables of n listed triplets (Fig. 1).
+ *   triplets    [n][3] int32 SNP indices, any three distinct, in the roles
+ *               X, Y, Z of the cell index 9 gX + 3 gY + gZ.
+ *   out_counts  [n][2][27] int32; row 0 controls, row 1 cases.
+ *   path        EPI3_PATH_AUTO or EPI3_PATH_POPC.
+ * Pointers are host memory unless the handle has EPI3_DEVICE_PTRS.
+ */
+int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,
+                int32_t path);
+
+/*
+ * Debug / test: K2 (Eq. 1) of n listed triplets, both as the scan's FP32 score
+ * (out_k2_f32, may be NULL) and as the FP64 rescoring value (out_k2_f64, may be
+ * NULL).  Triplets and pointer kinds as epi3_tables.
+ */
+int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k2_f32,
+                double* out_k2_f64);
+
+/*
+ * Options (strings): "path" = "auto" | "popc"; "threads" = threads per block of
+ * the scan kernel (64..512, multiple of 32); "ctas_per_sm" = persistent CTAs
+ * per SM (0 = occupancy maximum); "timing" = "0" | "1" (record CUDA events
+ * around the scan's kernels, read back with epi3_get_stats).
+ */
+int epi3_set_option(epi3_handle* h, const char* key, const char* value);
+
+/* Figures of the last scan of this handle. */
+typedef struct {
+    int64_t n_triplets;      /* triplets scored */
+    int64_t n_candidates;    /* FP32 candidates that reached the global stage */
+    int64_t n_rescored;      /* candidates recounted and rescored in FP64 */
+    float scan_kernel_ms;    /* counting + FP32 scoring kernel (timing = 1) */
+    float select_ms;         /* threshold selection + FP64 rescoring + final sort */
+    float total_ms;          /* whole scan, device time (timing = 1) */
+    float pack_ms;           /* class split + bit-plane packing at create (timing = 1) */
+    int32_t path;            /* EPI3_PATH_* used */
+    int32_t grid;            /* CTAs launched by the scan kernel */
+    int32_t block;           /* threads per CTA */
+    int32_t kernel_launches; /* kernels launched by the last scan */
+    float k2_rel_bound;      /* proven |FP32 - FP64| bound: rel * K2 + abs */
+    float k2_abs_bound;
+} epi3_stats;
+
+int epi3_get_stats(const epi3_handle* h, epi3_stats* out);
+
+/* Shape of a handle: M, N, controls, cases. */
+int epi3_get_shape(const epi3_handle* h, int32_t* n_snps, int32_t* n_samples,
+                   int32_t* n_controls, int32_t* n_cases);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPI3_H */

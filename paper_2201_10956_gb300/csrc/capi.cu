@@ -1,0 +1,524 @@
+// Host side of the C ABI (include/epi3.h): handles, validation, device memory, the
+// scan's launch sequence, error reporting and statistics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "epi3_internal.cuh"
+
+using namespace epi3;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(EPI3_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(EPI3_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                               \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Host-side fault injection for tests of the error paths: EPI3_FAULT=alloc makes the
+// next device allocation fail, EPI3_FAULT=launch makes the next scan launch fail.
+bool inject(const char* what) {
+    const char* f = getenv("EPI3_FAULT");
+    return f && strcmp(f, what) == 0;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (inject("alloc")) return cudaErrorMemoryAllocation;
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(p, bytes);
+}
+
+long long pairs(long long m) { return m < 2 ? 0 : m * (m - 1) / 2; }
+
+// Triplets (i, j, k), k > j, of the pairs with index in [pb, pe) (p = j(j-1)/2 + i).
+long long triplets_in_pairs(long long M, long long pb, long long pe) {
+    long long t = 0;
+    for (long long j = 1; j < M; ++j) {
+        const long long lo = j * (j - 1) / 2, hi = lo + j;
+        const long long a = pb > lo ? pb : lo, b = pe < hi ? pe : hi;
+        if (b > a) t += (b - a) * (M - 1 - j);
+    }
+    return t;
+}
+
+}  // namespace
+
+struct epi3_handle {
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int flags = 0;
+    int M = 0, N = 0, N0 = 0, N1 = 0;
+    Planes pl{};
+    uint4* d_planes = nullptr;
+    float2* d_lf2 = nullptr;
+    double* d_lf64 = nullptr;
+    K2Tables k2{};
+    int g_bits = 0;
+    Ctrl* d_ctrl = nullptr;
+    Cand* d_cand = nullptr;
+    long long cand_cap = 0;
+    Final* d_fin = nullptr;
+    double* d_out_scores = nullptr;
+    int* d_out_trip = nullptr;
+    Ctrl* h_ctrl = nullptr;       // pinned
+    double* h_scores = nullptr;   // pinned [EPI3_MAX_TOPK]
+    int* h_trip = nullptr;        // pinned [EPI3_MAX_TOPK * 3]
+    int path = EPI3_PATH_POPC;
+    int threads = 128;
+    int ctas_per_sm = 0;
+    bool timing = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    epi3_stats stats{};
+};
+
+namespace {
+
+void release(epi3_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_planes);
+    cudaFree(h->d_lf2);
+    cudaFree(h->d_lf64);
+    cudaFree(h->d_ctrl);
+    cudaFree(h->d_cand);
+    cudaFree(h->d_fin);
+    cudaFree(h->d_out_scores);
+    cudaFree(h->d_out_trip);
+    cudaFreeHost(h->h_ctrl);
+    cudaFreeHost(h->h_scores);
+    cudaFreeHost(h->h_trip);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int check_device(int* dev, int* sms) {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return fail(EPI3_ERR_UNSUPPORTED, "no CUDA device (%s)",
+                    e == cudaSuccess ? "count 0" : cudaGetErrorString(e));
+    CK(cudaGetDevice(dev), "cudaGetDevice");
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, *dev), "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(EPI3_ERR_UNSUPPORTED, "device %d is sm_%d%d; this build targets sm_103a only",
+                    *dev, prop.major, prop.minor);
+    *sms = prop.multiProcessorCount;
+    return EPI3_OK;
+}
+
+// Log-factorial tables of Eq. 1.  lf[n] = lf[n-1] + log(n) in FP64 (the same additions
+// in the same order as summing log b for b = 1..n).  The FP32 pair splits lf = hi + lo
+// with hi on the grid 2^-g, g the largest integer with lf[N+1] * 2^g < 2^23, so that
+// every hi difference and partial sum in k2_f32 is exact.
+int build_k2_tables(epi3_handle* h) {
+    const int n = h->N + 2;
+    std::vector<double> lf(n);
+    lf[0] = 0.0;
+    for (int i = 1; i < n; ++i) lf[i] = lf[i - 1] + std::log((double)i);
+    int e = 0;
+    std::frexp(lf[n - 1], &e);  // lf[N+1] < 2^e
+    const int g = 23 - e;
+    std::vector<float2> lf2(n);
+    for (int i = 0; i < n; ++i) {
+        const double hi = std::ldexp(std::nearbyint(std::ldexp(lf[i], g)), -g);
+        lf2[i].x = (float)hi;
+        lf2[i].y = (float)(lf[i] - hi);
+    }
+    h->g_bits = g;
+    CK(dev_alloc((void**)&h->d_lf64, sizeof(double) * n), "alloc lf64");
+    CK(dev_alloc((void**)&h->d_lf2, sizeof(float2) * n), "alloc lf2");
+    CK(cudaMemcpyAsync(h->d_lf64, lf.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream),
+       "upload lf64");
+    CK(cudaMemcpyAsync(h->d_lf2, lf2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->stream),
+       "upload lf2");
+    CK(cudaStreamSynchronize(h->stream), "sync lf upload");
+    h->k2.lf2 = h->d_lf2;
+    h->k2.lf64 = h->d_lf64;
+    h->k2.rel = std::ldexp(1.0f, -23);
+    h->k2.abs_ = std::ldexp(1.0f, -(g + 13));
+    return EPI3_OK;
+}
+
+int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
+    const size_t MN = (size_t)h->M * h->N;
+    uint8_t* d_geno = nullptr;
+    uint8_t* d_pheno = nullptr;
+    int* d_perm = nullptr;
+    int* d_counts = nullptr;
+    int rc = EPI3_OK;
+    auto cleanup = [&]() {
+        if (!(h->flags & EPI3_DEVICE_PTRS)) {
+            cudaFree(d_geno);
+            cudaFree(d_pheno);
+        }
+        cudaFree(d_perm);
+        cudaFree(d_counts);
+    };
+    do {
+        cudaError_t e;
+        if ((e = dev_alloc((void**)&h->d_ctrl, sizeof(Ctrl))) != cudaSuccess) { rc = cuda_fail(e, "alloc ctrl"); break; }
+        if ((e = cudaMallocHost((void**)&h->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { rc = cuda_fail(e, "pinned ctrl"); break; }
+        if (h->flags & EPI3_DEVICE_PTRS) {
+            d_geno = const_cast<uint8_t*>(geno);
+            d_pheno = const_cast<uint8_t*>(pheno);
+        } else {
+            if ((e = dev_alloc((void**)&d_geno, MN)) != cudaSuccess) { rc = cuda_fail(e, "alloc genotypes"); break; }
+            if ((e = dev_alloc((void**)&d_pheno, h->N)) != cudaSuccess) { rc = cuda_fail(e, "alloc phenotype"); break; }
+            if ((e = cudaMemcpyAsync(d_geno, geno, MN, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "copy genotypes"); break; }
+            if ((e = cudaMemcpyAsync(d_pheno, pheno, h->N, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "copy phenotype"); break; }
+        }
+        if ((e = dev_alloc((void**)&d_perm, sizeof(int) * h->N)) != cudaSuccess) { rc = cuda_fail(e, "alloc perm"); break; }
+        if ((e = dev_alloc((void**)&d_counts, sizeof(int) * 2)) != cudaSuccess) { rc = cuda_fail(e, "alloc counts"); break; }
+        if ((e = cudaEventRecord(h->ev[0], h->stream)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+        if ((e = launch_reset(h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "reset"); break; }
+        if ((e = launch_class_index(d_pheno, h->N, d_perm, d_counts, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index launch"); break; }
+        int counts[2] = {0, 0};
+        if ((e = cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read counts"); break; }
+        if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index"); break; }
+        if (h->h_ctrl->status & kStBadPhenotype) { rc = fail(EPI3_ERR_ARG, "phenotype value > 1"); break; }
+        h->N0 = counts[0];
+        h->N1 = counts[1];
+        Planes& pl = h->pl;
+        pl.M = h->M;
+        pl.W4[0] = (h->N0 + kSamplesPerGroup - 1) / kSamplesPerGroup;
+        pl.W4[1] = (h->N1 + kSamplesPerGroup - 1) / kSamplesPerGroup;
+        pl.coff[0] = 0;
+        pl.coff[1] = 2LL * pl.W4[0] * h->M;
+        pl.pad[0] = kSamplesPerGroup * pl.W4[0] - h->N0;
+        pl.pad[1] = kSamplesPerGroup * pl.W4[1] - h->N1;
+        const size_t n4 = 2ull * (pl.W4[0] + pl.W4[1]) * h->M;
+        if ((e = dev_alloc((void**)&h->d_planes, n4 * sizeof(uint4))) != cudaSuccess) { rc = cuda_fail(e, "alloc planes"); break; }
+        pl.planes = h->d_planes;
+        if ((e = launch_pack(d_geno, h->M, h->N, d_perm, h->N0, h->N1, pl, h->d_planes, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "pack launch"); break; }
+        if ((e = cudaEventRecord(h->ev[1], h->stream)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+        if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "pack"); break; }
+        if (h->h_ctrl->status & kStBadGenotype) { rc = fail(EPI3_ERR_ARG, "genotype value > 2"); break; }
+        cudaEventElapsedTime(&h->stats.pack_ms, h->ev[0], h->ev[1]);
+    } while (0);
+    cleanup();
+    if (rc != EPI3_OK) return rc;
+    if ((rc = build_k2_tables(h)) != EPI3_OK) return rc;
+    h->cand_cap = 1LL << 16;
+    CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "alloc candidates");
+    CK(dev_alloc((void**)&h->d_fin, sizeof(Final) * kFinalCap), "alloc final");
+    CK(dev_alloc((void**)&h->d_out_scores, sizeof(double) * EPI3_MAX_TOPK), "alloc out scores");
+    CK(dev_alloc((void**)&h->d_out_trip, sizeof(int) * 3 * EPI3_MAX_TOPK), "alloc out triplets");
+    CK(cudaMallocHost((void**)&h->h_scores, sizeof(double) * EPI3_MAX_TOPK), "pinned scores");
+    CK(cudaMallocHost((void**)&h->h_trip, sizeof(int) * 3 * EPI3_MAX_TOPK), "pinned triplets");
+    return EPI3_OK;
+}
+
+int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* out_trip,
+              double* out_scores, int32_t* n_out, bool exact_k) {
+    if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    if (!out_trip || !out_scores) return fail(EPI3_ERR_ARG, "null output pointer");
+    const long long np = pairs(h->M - 1);  // pairs with j <= M-2 (j = M-1 has no k)
+    if (pb < 0 || pe < pb) return fail(EPI3_ERR_ARG, "bad pair range [%lld, %lld)", pb, pe);
+    if (pe > np) pe = np;
+    if (pb > pe) pb = pe;
+    const long long nt = triplets_in_pairs(h->M, pb, pe);
+    if (top_k < 1 || top_k > EPI3_MAX_TOPK)
+        return fail(EPI3_ERR_ARG, "top_k %d outside 1..%d", top_k, EPI3_MAX_TOPK);
+    if (top_k > nt) {
+        if (exact_k) return fail(EPI3_ERR_ARG, "top_k %d > %lld triplets", top_k, nt);
+        top_k = (int)nt;
+    }
+    if (n_out) *n_out = 0;
+    if (top_k == 0) return EPI3_OK;
+    if (h->path != EPI3_PATH_POPC && h->path != EPI3_PATH_AUTO)
+        return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", h->path);
+
+    const int block = h->threads;
+    const size_t smem = scan_popc_smem(h->pl);
+    int occ = 0;
+    CK(scan_popc_occupancy(block, smem, &occ), "scan occupancy");
+    if (occ < 1) return fail(EPI3_ERR_UNSUPPORTED, "scan kernel does not fit (smem %zu)", smem);
+    const int per_sm = h->ctas_per_sm > 0 && h->ctas_per_sm < occ ? h->ctas_per_sm : occ;
+    const int grid = h->sm_count * per_sm;
+
+    for (int attempt = 0;; ++attempt) {
+        if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
+        CK(cudaEventRecord(h->ev[0], h->stream), "event");
+        CK(launch_reset(h->d_ctrl, h->stream), "reset launch");
+        ScanArgs a;
+        a.pl = h->pl;
+        a.k2 = h->k2;
+        a.ctrl = h->d_ctrl;
+        a.cand = h->d_cand;
+        a.cand_cap = h->cand_cap;
+        a.pair_begin = pb;
+        a.pair_end = pe;
+        a.top_k = top_k;
+        CK(cudaEventRecord(h->ev[1], h->stream), "event");
+        CK(launch_scan_popc(a, grid, block, smem, h->stream), "scan launch");
+        CK(cudaEventRecord(h->ev[2], h->stream), "event");
+        CK(launch_select(h->d_ctrl, h->d_cand, h->cand_cap, top_k, h->k2.rel, h->k2.abs_, h->stream),
+           "select launch");
+        CK(launch_rescore(h->pl, h->k2, h->d_ctrl, h->d_cand, h->cand_cap, h->d_fin,
+                          h->sm_count * 8, h->stream),
+           "rescore launch");
+        CK(launch_final(h->d_ctrl, h->d_fin, top_k, h->d_out_scores, h->d_out_trip, h->stream),
+           "final launch");
+        CK(cudaEventRecord(h->ev[3], h->stream), "event");
+        CK(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream),
+           "read status");
+        if (!(h->flags & EPI3_DEVICE_PTRS)) {
+            CK(cudaMemcpyAsync(h->h_scores, h->d_out_scores, sizeof(double) * top_k,
+                               cudaMemcpyDeviceToHost, h->stream), "read scores");
+            CK(cudaMemcpyAsync(h->h_trip, h->d_out_trip, sizeof(int) * 3 * top_k,
+                               cudaMemcpyDeviceToHost, h->stream), "read triplets");
+        }
+        CK(cudaStreamSynchronize(h->stream), "scan");
+        const int st = h->h_ctrl->status;
+        if (st & kStCandOverflow) {
+            if (h->cand_cap >= (1LL << 24) || attempt >= 3)
+                return fail(EPI3_ERR_OVERFLOW, "more than %lld FP32 candidates", h->cand_cap);
+            cudaFree(h->d_cand);
+            h->d_cand = nullptr;
+            h->cand_cap *= 8;
+            CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
+            continue;
+        }
+        if (st & kStFinalOverflow)
+            return fail(EPI3_ERR_OVERFLOW,
+                        "more than %d triplets lie within the FP32 error band of the k-th best",
+                        kFinalCap);
+        if (st & (kStInternal | kStBadIndex))
+            return fail(EPI3_ERR_CUDA, "internal error in the candidate stage (status %d)", st);
+        break;
+    }
+    const int nout = (int)h->h_ctrl->n_out;
+    if (h->flags & EPI3_DEVICE_PTRS) {
+        CK(cudaMemcpyAsync(out_scores, h->d_out_scores, sizeof(double) * nout,
+                           cudaMemcpyDeviceToDevice, h->stream), "copy scores");
+        CK(cudaMemcpyAsync(out_trip, h->d_out_trip, sizeof(int) * 3 * nout,
+                           cudaMemcpyDeviceToDevice, h->stream), "copy triplets");
+        CK(cudaStreamSynchronize(h->stream), "copy outputs");
+    } else {
+        memcpy(out_scores, h->h_scores, sizeof(double) * nout);
+        memcpy(out_trip, h->h_trip, sizeof(int) * 3 * nout);
+    }
+    if (n_out) *n_out = nout;
+    epi3_stats& s = h->stats;
+    s.n_triplets = nt;
+    s.n_candidates = h->h_ctrl->n_cand;
+    s.n_rescored = h->h_ctrl->n_final;
+    s.path = EPI3_PATH_POPC;
+    s.grid = grid;
+    s.block = block;
+    s.kernel_launches = 5;
+    s.k2_rel_bound = h->k2.rel;
+    s.k2_abs_bound = h->k2.abs_;
+    cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
+    return EPI3_OK;
+}
+
+int per_triplet(epi3_handle* h, long long n, const int32_t* trip, int32_t* out_counts,
+                float* out_s32, double* out_s64) {
+    if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    if (n < 0 || (n > 0 && !trip)) return fail(EPI3_ERR_ARG, "bad triplet list");
+    if (n == 0) return EPI3_OK;
+    const bool dev = (h->flags & EPI3_DEVICE_PTRS) != 0;
+    int* d_trip = nullptr;
+    int* d_counts = nullptr;
+    float* d_s32 = nullptr;
+    double* d_s64 = nullptr;
+    int rc = EPI3_OK;
+    do {
+        cudaError_t e;
+        if (dev) {
+            d_trip = const_cast<int*>(trip);
+            d_counts = out_counts;
+            d_s32 = out_s32;
+            d_s64 = out_s64;
+        } else {
+            if ((e = dev_alloc((void**)&d_trip, sizeof(int) * 3 * n)) != cudaSuccess) { rc = cuda_fail(e, "alloc triplets"); break; }
+            if ((e = cudaMemcpyAsync(d_trip, trip, sizeof(int) * 3 * n, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "copy triplets"); break; }
+            if (out_counts && (e = dev_alloc((void**)&d_counts, sizeof(int) * 54 * n)) != cudaSuccess) { rc = cuda_fail(e, "alloc counts"); break; }
+            if (out_s32 && (e = dev_alloc((void**)&d_s32, sizeof(float) * n)) != cudaSuccess) { rc = cuda_fail(e, "alloc s32"); break; }
+            if (out_s64 && (e = dev_alloc((void**)&d_s64, sizeof(double) * n)) != cudaSuccess) { rc = cuda_fail(e, "alloc s64"); break; }
+        }
+        if ((e = launch_reset(h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "reset"); break; }
+        const bool k2 = out_s32 || out_s64;
+        if ((e = launch_tables(h->pl, k2 ? &h->k2 : nullptr, n, d_trip, d_counts, d_s32, d_s64, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "tables launch"); break; }
+        if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
+        if (!dev) {
+            if (out_counts && (e = cudaMemcpyAsync(out_counts, d_counts, sizeof(int) * 54 * n, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read counts"); break; }
+            if (out_s32 && (e = cudaMemcpyAsync(out_s32, d_s32, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read s32"); break; }
+            if (out_s64 && (e = cudaMemcpyAsync(out_s64, d_s64, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read s64"); break; }
+        }
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "tables"); break; }
+        if (h->h_ctrl->status & kStBadIndex) rc = fail(EPI3_ERR_ARG, "triplet index outside 0..%d", h->M - 1);
+    } while (0);
+    if (!dev) {
+        cudaFree(d_trip);
+        cudaFree(d_counts);
+        cudaFree(d_s32);
+        cudaFree(d_s64);
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* epi3_last_error(void) { return g_err.c_str(); }
+
+int epi3_create(epi3_handle** out, const uint8_t* genotypes, const uint8_t* phenotype,
+                int32_t n_snps, int32_t n_samples, int32_t flags, void* cuda_stream) {
+    g_err.clear();
+    if (!out) return fail(EPI3_ERR_ARG, "null handle pointer");
+    *out = nullptr;
+    if (!genotypes || !phenotype) return fail(EPI3_ERR_ARG, "null genotypes or phenotype");
+    if (n_snps < 3) return fail(EPI3_ERR_ARG, "n_snps %d < 3", n_snps);
+    if (n_snps >= (1 << 21)) return fail(EPI3_ERR_ARG, "n_snps %d >= 2^21", n_snps);
+    if (n_samples < 1) return fail(EPI3_ERR_ARG, "n_samples %d < 1", n_samples);
+    if (n_samples > kMaxSamples)
+        return fail(EPI3_ERR_UNSUPPORTED, "n_samples %d > %d", n_samples, kMaxSamples);
+    if (flags & ~EPI3_DEVICE_PTRS) return fail(EPI3_ERR_ARG, "unknown flags 0x%x", flags);
+    int dev = 0, sms = 0;
+    int rc = check_device(&dev, &sms);
+    if (rc != EPI3_OK) return rc;
+    epi3_handle* h = new epi3_handle();
+    h->device = dev;
+    h->sm_count = sms;
+    h->flags = flags;
+    h->M = n_snps;
+    h->N = n_samples;
+    cudaError_t e;
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        release(h);
+        return cuda_fail(e, "stream create");
+    } else {
+        h->own_stream = true;
+    }
+    for (auto& ev : h->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+            release(h);
+            return cuda_fail(e, "event create");
+        }
+    rc = create_impl(h, genotypes, phenotype);
+    if (rc != EPI3_OK) {
+        std::string msg = g_err;
+        release(h);
+        g_err = msg;
+        return rc;
+    }
+    *out = h;
+    return EPI3_OK;
+}
+
+int epi3_destroy(epi3_handle* h) {
+    g_err.clear();
+    release(h);
+    return EPI3_OK;
+}
+
+int epi3_scan(epi3_handle* h, int32_t top_k, int32_t* out_triplets, double* out_scores) {
+    g_err.clear();
+    if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    return scan_impl(h, 0, pairs(h->M), top_k, out_triplets, out_scores, nullptr, true);
+}
+
+int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_t top_k,
+                    int32_t* out_triplets, double* out_scores, int32_t* n_out) {
+    g_err.clear();
+    return scan_impl(h, pair_begin, pair_end, top_k, out_triplets, out_scores, n_out, false);
+}
+
+int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,
+                int32_t path) {
+    g_err.clear();
+    if (path != EPI3_PATH_AUTO && path != EPI3_PATH_POPC)
+        return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
+    if (n > 0 && !out_counts) return fail(EPI3_ERR_ARG, "null out_counts");
+    return per_triplet(h, n, triplets, out_counts, nullptr, nullptr);
+}
+
+int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k2_f32,
+                double* out_k2_f64) {
+    g_err.clear();
+    if (n > 0 && !out_k2_f32 && !out_k2_f64) return fail(EPI3_ERR_ARG, "no output requested");
+    return per_triplet(h, n, triplets, nullptr, out_k2_f32, out_k2_f64);
+}
+
+int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
+    g_err.clear();
+    if (!h || !key || !value) return fail(EPI3_ERR_ARG, "null argument");
+    if (!strcmp(key, "path")) {
+        if (!strcmp(value, "auto")) h->path = EPI3_PATH_AUTO;
+        else if (!strcmp(value, "popc")) h->path = EPI3_PATH_POPC;
+        else return fail(EPI3_ERR_UNSUPPORTED, "path '%s' not available", value);
+        return EPI3_OK;
+    }
+    if (!strcmp(key, "threads")) {
+        const int v = atoi(value);
+        if (v < 64 || v > 256 || v % 32) return fail(EPI3_ERR_ARG, "threads %d not in 64..256 step 32", v);
+        h->threads = v;
+        return EPI3_OK;
+    }
+    if (!strcmp(key, "ctas_per_sm")) {
+        const int v = atoi(value);
+        if (v < 0 || v > 32) return fail(EPI3_ERR_ARG, "ctas_per_sm %d not in 0..32", v);
+        h->ctas_per_sm = v;
+        return EPI3_OK;
+    }
+    if (!strcmp(key, "timing")) {
+        h->timing = atoi(value) != 0;
+        return EPI3_OK;
+    }
+    return fail(EPI3_ERR_ARG, "unknown option '%s'", key);
+}
+
+int epi3_get_stats(const epi3_handle* h, epi3_stats* out) {
+    if (!h || !out) return fail(EPI3_ERR_ARG, "null argument");
+    *out = h->stats;
+    return EPI3_OK;
+}
+
+int epi3_get_shape(const epi3_handle* h, int32_t* n_snps, int32_t* n_samples,
+                   int32_t* n_controls, int32_t* n_cases) {
+    if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    if (n_snps) *n_snps = h->M;
+    if (n_samples) *n_samples = h->N;
+    if (n_controls) *n_controls = h->N0;
+    if (n_cases) *n_cases = h->N1;
+    return EPI3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+"""Python binding of the epi3 C ABI (include/epi3.h): argument marshalling only.
+
+Every step of the scan runs in the CUDA library ``libepi3.so`` built next to this
+file.  There is no fallback: if the library is missing or no sm_103 GPU is
+present, calls raise ``Epi3Error``.
+
+Inputs may be numpy arrays (host memory; results come back as numpy arrays) or
+CUDA torch tensors (device memory, ``EPI3_DEVICE_PTRS``; results come back as
+CUDA tensors).  torch is used only for device buffers and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libepi3.so")
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OVERFLOW = -1, -2, -3, -4, -5, -6
+DEVICE_PTRS = 1
+PATH_AUTO, PATH_POPC = 0, 1
+MAX_TOPK = 512
+
+# Every symbol the header declares; tests check the library exports all of them.
+SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_destroy", "epi3_last_error",
+           "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape")
+
+
+class Epi3Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"epi3 error {code}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_triplets", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("n_rescored", ctypes.c_int64), ("scan_kernel_ms", ctypes.c_float),
+                ("select_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("pack_ms", ctypes.c_float), ("path", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("k2_rel_bound", ctypes.c_float), ("k2_abs_bound", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libepi3.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise Epi3Error(ERR_UNSUPPORTED,
+                        f"{path} not built; run `python -m paper_2201_10956_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "epi3_create": [ctypes.POINTER(P), P, P, I32, I32, I32, P],
+        "epi3_scan": [P, I32, P, P],
+        "epi3_scan_range": [P, I64, I64, I32, P, P, ctypes.POINTER(I32)],
+        "epi3_destroy": [P],
+        "epi3_last_error": [],
+        "epi3_tables": [P, I64, P, P, I32],
+        "epi3_scores": [P, I64, P, P, P],
+        "epi3_set_option": [P, ctypes.c_char_p, ctypes.c_char_p],
+        "epi3_get_stats": [P, ctypes.POINTER(Stats)],
+        "epi3_get_shape": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                           ctypes.POINTER(I32)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "epi3_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().epi3_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise Epi3Error(rc, last_error())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+class Handle:
+    """One packed data set on the GPU (epi3_create / epi3_destroy)."""
+
+    def __init__(self, genotypes, phenotype, stream=None):
+        lib = load()
+        self._dev = _is_torch(genotypes)
+        if self._dev:
+            import torch
+            if not (genotypes.is_cuda and phenotype.is_cuda):
+                raise Epi3Error(ERR_ARG, "torch inputs must be CUDA tensors")
+            g = genotypes.contiguous().to(torch.uint8)
+            p = phenotype.contiguous().to(torch.uint8)
+            if stream is None:
+                stream = torch.cuda.current_stream(g.device)
+            self._keep = (g, p)
+            m, n = g.shape
+        else:
+            g = np.ascontiguousarray(genotypes, dtype=np.uint8)
+            p = np.ascontiguousarray(phenotype, dtype=np.uint8)
+            m, n = g.shape
+        if p.shape[0] != n:
+            raise Epi3Error(ERR_ARG, "phenotype length does not match genotypes")
+        sptr = None
+        if stream is not None:
+            sptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.epi3_create(ctypes.byref(h), _ptr(g), _ptr(p), int(m), int(n),
+                               DEVICE_PTRS if self._dev else 0, sptr))
+        self._h = h
+        self._keep = None  # packed planes are owned by the handle
+        self.n_snps, self.n_samples = int(m), int(n)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().epi3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers
+    def _alloc(self, shape, dtype):
+        if self._dev:
+            import torch
+            tdt = {np.int32: torch.int32, np.float64: torch.float64, np.float32: torch.float32}[dtype]
+            return torch.empty(shape, dtype=tdt, device="cuda")
+        return np.empty(shape, dtype=dtype)
+
+    def _triplets(self, triplets):
+        if self._dev:
+            import torch
+            t = torch.as_tensor(triplets, dtype=torch.int32, device="cuda").reshape(-1, 3).contiguous()
+        else:
+            t = np.ascontiguousarray(triplets, dtype=np.int32).reshape(-1, 3)
+        return t
+
+    # -- API
+    def scan(self, top_k: int):
+        """Top-k triplets (int32 [k, 3]) and FP64 K2 scores ([k]), ascending."""
+        trip = self._alloc((top_k, 3), np.int32)
+        sc = self._alloc((top_k,), np.float64)
+        _check(load().epi3_scan(self._h, int(top_k), _ptr(trip), _ptr(sc)))
+        return trip, sc
+
+    def scan_range(self, pair_begin: int, pair_end: int, top_k: int):
+        trip = self._alloc((top_k, 3), np.int32)
+        sc = self._alloc((top_k,), np.float64)
+        n = ctypes.c_int32(0)
+        _check(load().epi3_scan_range(self._h, int(pair_begin), int(pair_end), int(top_k),
+                                      _ptr(trip), _ptr(sc), ctypes.byref(n)))
+        return trip[: n.value], sc[: n.value]
+
+    def tables(self, triplets, path: int = PATH_AUTO):
+        t = self._triplets(triplets)
+        out = self._alloc((t.shape[0], 2, 27), np.int32)
+        _check(load().epi3_tables(self._h, int(t.shape[0]), _ptr(t), _ptr(out), int(path)))
+        return out
+
+    def scores(self, triplets):
+        """(FP32 K2 as the scan computes it, FP64 K2 as the rescoring computes it)."""
+        t = self._triplets(triplets)
+        s32 = self._alloc((t.shape[0],), np.float32)
+        s64 = self._alloc((t.shape[0],), np.float64)
+        _check(load().epi3_scores(self._h, int(t.shape[0]), _ptr(t), _ptr(s32), _ptr(s64)))
+        return s32, s64
+
+    def set_option(self, key: str, value):
+        _check(load().epi3_set_option(self._h, key.encode(), str(value).encode()))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().epi3_get_stats(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def shape(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(load().epi3_get_shape(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+
+def pairs_of(m: int) -> int:
+    return m * (m - 1) // 2
