@@ -164,6 +164,8 @@ int build_k2_tables(epi3_handle* h) {
     h->k2.lf64 = h->d_lf64;
     h->k2.rel = std::ldexp(1.0f, -23);
     h->k2.abs_ = std::ldexp(1.0f, -(g + 13));
+    h->stats.k2_rel_bound = h->k2.rel;
+    h->stats.k2_abs_bound = h->k2.abs_;
     return EPI3_OK;
 }
 
