@@ -183,6 +183,18 @@ scan_popc27_kernel(const ScanArgs a) {
             }
         }
     }
+    // Before the final flush, cut the buffer to this CTA's own band: a CTA that never
+    // filled its buffer would otherwise flush every triplet it scored.
+    if (cnt >= a.top_k) {
+        for (int idx = cnt + tid; idx < kCtaCand; idx += nt) cbuf[idx].s = kInf;
+        __syncthreads();
+        sort_cands(cbuf);
+        if (tid == 0) {
+            const float tl = band_threshold(cbuf[a.top_k - 1].s, a.k2.rel, a.k2.abs_);
+            atomicMin(&a.ctrl->thr, __float_as_uint(tl));
+            s_tloc = fminf(s_tloc, tl);
+        }
+    }
     __syncthreads();
     const float t = fminf(s_tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr));
     flush_cands(a, cbuf, cnt, t);
