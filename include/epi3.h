@@ -158,6 +158,35 @@ typedef struct {
 
 int epi3_get_stats(const epi3_handle* h, epi3_stats* out);
 
+/*
+ * The whole scan (epi3_create + epi3_scan + epi3_destroy) without allocating memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while a CUDA graph is being captured, hosts with a fixed
+ * memory budget, or frameworks whose own caching allocator owns the device memory (a raw
+ * cudaMalloc/cudaFree there may fail or implicitly synchronise the device).
+ *
+ *   genotypes, phenotype   device pointers, same layout and values as epi3_create.
+ *   n_snps, n_samples      M >= 3, 1 <= N <= 65536, and the packed planes, tables and
+ *                          candidate lists must fit EPI3_NOALLOC_SCRATCH_BYTES (8 MiB:
+ *                          about M * N <= 2.5e7, e.g. 1024 x 20000); larger sizes are
+ *                          rejected with EPI3_ERR_ARG before any work is issued.
+ *   top_k, out_triplets, out_scores   as epi3_scan, but the outputs are device pointers.
+ *   cuda_stream            stream to run on (NULL = the legacy default stream).
+ *
+ * All scratch lives in one file-scope __device__ array of EPI3_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current, so
+ * make the first call on each device before any stream capture.  Calls share the array and
+ * it keeps the last call's contents; each call re-initialises what it reads.  Calls are
+ * serialised on the host and return when the results are written; calls that overlap on
+ * the GPU would race on the array.  The candidate list cannot grow: a data set with more
+ * near-tied FP32 candidates than it holds gives EPI3_ERR_OVERFLOW (use epi3_scan).
+ */
+#define EPI3_NOALLOC_SCRATCH_BYTES (8u << 20)
+int epi3_scan_noalloc(const uint8_t* genotypes, const uint8_t* phenotype, int32_t n_snps,
+                      int32_t n_samples, int32_t top_k, int32_t* out_triplets,
+                      double* out_scores, void* cuda_stream);
+
 /* Shape of a handle: M, N, controls, cases. */
 int epi3_get_shape(const epi3_handle* h, int32_t* n_snps, int32_t* n_samples,
                    int32_t* n_controls, int32_t* n_cases);

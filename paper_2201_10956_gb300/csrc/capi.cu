@@ -395,6 +395,8 @@ int per_triplet(epi3_handle* h, long long n, const int32_t* trip, int32_t* out_c
 
 }  // namespace
 
+void epi3::set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* epi3_last_error(void) { return g_err.c_str(); }

@@ -94,6 +94,9 @@ cudaError_t launch_tables(const Planes& pl, const K2Tables* k2, long long n, con
                           cudaStream_t st);
 cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
 
+// Message returned by epi3_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // ---------------------------------------------------------------- device helpers
 
 // Upper end of the FP32 band that can still hold the answer, given the k-th best

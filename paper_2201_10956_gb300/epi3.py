@@ -26,7 +26,8 @@ MAX_TOPK = 512
 
 # Every symbol the header declares; tests check the library exports all of them.
 SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_destroy", "epi3_last_error",
-           "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape")
+           "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
+           "epi3_scan_noalloc")
 
 
 class Epi3Error(RuntimeError):
@@ -69,6 +70,7 @@ def load(path: str = LIB_PATH):
         "epi3_get_stats": [P, ctypes.POINTER(Stats)],
         "epi3_get_shape": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
                            ctypes.POINTER(I32)],
+        "epi3_scan_noalloc": [P, P, I32, I32, I32, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -208,6 +210,25 @@ class Handle:
         v = [ctypes.c_int32() for _ in range(4)]
         _check(load().epi3_get_shape(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+
+def scan_noalloc(genotypes, phenotype, top_k: int, stream=None):
+    """epi3_scan_noalloc on CUDA tensors: the scan with no memory allocated by the library.
+
+    For callers that cannot allocate (graph capture, fixed memory budgets, foreign
+    allocators); the outputs are allocated here by torch, the scratch is the library's
+    static device array (8 MiB).  Returns (triplets int32 [k, 3], scores float64 [k]) on
+    the device.
+    """
+    import torch
+    m, n = genotypes.shape
+    trip = torch.empty((top_k, 3), dtype=torch.int32, device=genotypes.device)
+    sc = torch.empty((top_k,), dtype=torch.float64, device=genotypes.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(genotypes.device)
+    _check(load().epi3_scan_noalloc(_ptr(genotypes), _ptr(phenotype), int(m), int(n), int(top_k),
+                                    _ptr(trip), _ptr(sc), ctypes.c_void_p(stream.cuda_stream)))
+    return trip, sc
 
 
 def pairs_of(m: int) -> int:
