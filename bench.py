@@ -288,13 +288,15 @@ def run_ours(args, rank, world, local_rank):
     peaks = read_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     kern_s = statistics.mean(kern_ms) / 1000.0
-    popc_alg = gen.n_triplets(m) * n * 27.0 / 32.0     # 32-bit POPC per launch (27-cell form)
+    cells = 8.0 if st["path"] == 2 else 27.0            # POPC per 32-sample word and class
+    popc_alg = gen.n_triplets(m) * n * cells / 32.0     # 32-bit POPC per launch
     if world > 1:
         popc_alg /= world
     peak_popc = props.multi_processor_count * sm_max * 1e6 * POPC_PER_SM_CLK
     achieved = popc_alg / kern_s
     traffic = TRAFFIC.get((args.path, args.config))
-    roofline = {"bound": "alu", "kernel": "scan_popc27_kernel", "achieved": achieved / 1e12,
+    kname = "scan_popc_kernel<true> (8-cell)" if st["path"] == 2 else "scan_popc_kernel<false> (27-cell)"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
                 "peak": peak_popc / 1e12, "unit": "TPOPC/s", "frac": achieved / peak_popc,
                 "traffic": traffic,
                 "peak_note": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
@@ -322,7 +324,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="large")
-    ap.add_argument("--path", default="popc")
+    ap.add_argument("--path", default="auto")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

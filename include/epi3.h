@@ -38,7 +38,7 @@ extern "C" {
 #define EPI3_ERR_ARG (-1)         /* bad pointer, size, genotype > 2, phenotype > 1, top_k */
 #define EPI3_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
 #define EPI3_ERR_OOM (-3)         /* device or pinned host allocation failed */
-#define EPI3_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out */
+#define EPI3_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out (1 s) */
 #define EPI3_ERR_UNSUPPORTED (-5) /* no sm_103 device, or a path/size this build lacks */
 #define EPI3_ERR_OVERFLOW (-6)    /* more near-tied candidates than the candidate stage holds */
 
@@ -47,7 +47,12 @@ extern "C" {
 
 /* counting paths (epi3_tables, option "path") */
 #define EPI3_PATH_AUTO 0
-#define EPI3_PATH_POPC 1 /* 27-cell LOP3 AND + POPC over bit planes (Alg. 2 counting) */
+#define EPI3_PATH_POPC 1  /* 27-cell LOP3 AND + POPC over bit planes (Alg. 2 counting) */
+#define EPI3_PATH_POPC8 2 /* 8 cells (genotypes 0/1) by AND + POPC, 19 derived exactly from
+                             pair tables and marginals; the default (auto) scan path */
+#define EPI3_PATH_MMA 3   /* tensor cores: the 8 cells as a GEMM of one-hot 0/1 E4M3 operands
+                             (tcgen05 kind::f8f6f4, FP32 accumulation), 19 derived */
+#define EPI3_PATH_MMA16 4 /* the same GEMM with FP16 operands (tcgen05 kind::f16) */
 
 #define EPI3_MAX_TOPK 512
 
@@ -117,7 +122,8 @@ const char* epi3_last_error(void);
  *   triplets    [n][3] int32 SNP indices, any three distinct, in the roles
  *               X, Y, Z of the cell index 9 gX + 3 gY + gZ.
  *   out_counts  [n][2][27] int32; row 0 controls, row 1 cases.
- *   path        EPI3_PATH_AUTO or EPI3_PATH_POPC.
+ *   path        EPI3_PATH_AUTO (= POPC: direct 27-cell count) or EPI3_PATH_POPC8
+ *               (8 cells counted, 19 derived; needs three distinct SNPs).
  * Pointers are host memory unless the handle has EPI3_DEVICE_PTRS.
  */
 int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,
@@ -132,7 +138,8 @@ int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k
                 double* out_k2_f64);
 
 /*
- * Options (strings): "path" = "auto" | "popc"; "threads" = threads per block of
+ * Options (strings): "path" = "auto" | "popc" | "popc8" | "mma" | "mma16"; "threads" =
+ * threads per block of
  * the scan kernel (64..512, multiple of 32); "ctas_per_sm" = persistent CTAs
  * per SM (0 = occupancy maximum); "timing" = "0" | "1" (record CUDA events
  * around the scan's kernels, read back with epi3_get_stats).

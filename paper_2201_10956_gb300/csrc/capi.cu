@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -85,6 +86,15 @@ struct epi3_handle {
     Final* d_fin = nullptr;
     double* d_out_scores = nullptr;
     int* d_out_trip = nullptr;
+    int4* d_pt = nullptr;         // pair tables (8-cell forms), built on first use
+    int2* d_marg = nullptr;
+    PairTables ptab{};
+    uint8_t* d_oh = nullptr;      // pre-tiled one-hot operand of the tensor-core form
+    int oh_fp8 = -1;              // element type d_oh was built for (-1: none)
+    int oh_ks[2] = {0, 0};
+    long long oh_off1 = 0;
+    int4* d_tiles = nullptr;      // tile list of the tensor-core form
+    long long n_tiles = 0, tiles_pb = -1, tiles_pe = -1;
     Ctrl* h_ctrl = nullptr;       // pinned
     double* h_scores = nullptr;   // pinned [EPI3_MAX_TOPK]
     int* h_trip = nullptr;        // pinned [EPI3_MAX_TOPK * 3]
@@ -109,6 +119,10 @@ void release(epi3_handle* h) {
     cudaFree(h->d_fin);
     cudaFree(h->d_out_scores);
     cudaFree(h->d_out_trip);
+    cudaFree(h->d_pt);
+    cudaFree(h->d_marg);
+    cudaFree(h->d_oh);
+    cudaFree(h->d_tiles);
     cudaFreeHost(h->h_ctrl);
     cudaFreeHost(h->h_scores);
     cudaFreeHost(h->h_trip);
@@ -240,6 +254,170 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     return EPI3_OK;
 }
 
+// Pair tables and marginals of the 8-cell forms (built once per handle).
+int ensure_pair_tables(epi3_handle* h) {
+    if (h->d_pt) return EPI3_OK;
+    const long long np = pairs(h->M);
+    CK(dev_alloc((void**)&h->d_pt, sizeof(int4) * 2 * (size_t)np), "alloc pair tables");
+    CK(dev_alloc((void**)&h->d_marg, sizeof(int2) * 2 * (size_t)h->M), "alloc marginals");
+    CK(launch_pair_tables(h->pl, h->d_pt, h->d_marg, np, h->stream), "pair tables launch");
+    CK(cudaStreamSynchronize(h->stream), "pair tables");
+    h->ptab.pt = h->d_pt;
+    h->ptab.marg = h->d_marg;
+    h->ptab.n_pairs = np;
+    h->ptab.n_c[0] = h->N0;
+    h->ptab.n_c[1] = h->N1;
+    return EPI3_OK;
+}
+
+// Tensor-core form: pre-tiled one-hot operand (built once per element type).
+int ensure_onehot(epi3_handle* h, bool fp8) {
+    if (h->d_oh && h->oh_fp8 == (fp8 ? 1 : 0)) return EPI3_OK;
+    cudaFree(h->d_oh);
+    h->d_oh = nullptr;
+    const int spk = mma_samples_per_step(fp8);
+    const int ks0 = (h->N0 + spk - 1) / spk, ks1 = (h->N1 + spk - 1) / spk;
+    const int kbc = (h->M + 63) / 64;
+    const size_t bytes = (size_t)kbc * (ks0 + ks1) * 16384;
+    CK(dev_alloc((void**)&h->d_oh, bytes), "alloc one-hot operand");
+    h->oh_ks[0] = ks0;
+    h->oh_ks[1] = ks1;
+    h->oh_off1 = (long long)kbc * ks0;
+    CK(launch_onehot(h->pl, h->d_oh, h->oh_off1, ks0, ks1, kbc, fp8, h->stream), "one-hot launch");
+    CK(cudaStreamSynchronize(h->stream), "one-hot");
+    h->oh_fp8 = fp8 ? 1 : 0;
+    return EPI3_OK;
+}
+
+// Tiles (i, 32-SNP block of j, 64-SNP block of k) holding a triplet i<j<k whose pair (i, j)
+// lies in [pb, pe); third-SNP block outermost so concurrent CTAs share A chunks in L2.
+int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
+    if (h->d_tiles && h->tiles_pb == pb && h->tiles_pe == pe) return EPI3_OK;
+    cudaFree(h->d_tiles);
+    h->d_tiles = nullptr;
+    const int M = h->M, kbc = (M + 63) / 64, jbc = (M + 31) / 32;
+    std::vector<int4> t;
+    for (int kb = 0; kb < kbc; ++kb) {
+        const int k_hi = std::min(64 * kb + 63, M - 1);
+        for (int jb = 0; jb < jbc; ++jb) {
+            const int j_lo = 32 * jb, j_hi = std::min(32 * jb + 31, M - 1);
+            if (j_lo >= k_hi) continue;
+            const int i_end = std::min(j_hi, k_hi - 1);
+            for (int i = 0; i < i_end; ++i) {
+                const long long jmin = std::max(j_lo, i + 1), jmax = std::min(j_hi, k_hi - 1);
+                const long long pmin = jmin * (jmin - 1) / 2 + i, pmax = jmax * (jmax - 1) / 2 + i;
+                if (pmin >= pe || pmax < pb) continue;
+                t.push_back(make_int4(i, jb, kb, 0));
+            }
+        }
+    }
+    h->n_tiles = (long long)t.size();
+    CK(dev_alloc((void**)&h->d_tiles, sizeof(int4) * (t.empty() ? 1 : t.size())), "alloc tiles");
+    if (!t.empty())
+        CK(cudaMemcpyAsync(h->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice,
+                           h->stream), "upload tiles");
+    CK(cudaStreamSynchronize(h->stream), "tiles");
+    h->tiles_pb = pb;
+    h->tiles_pe = pe;
+    return EPI3_OK;
+}
+
+int resolve_path(const epi3_handle* h) {
+    return h->path == EPI3_PATH_AUTO ? EPI3_PATH_POPC8 : h->path;
+}
+
+// Candidate stage + result read-back shared by both scan forms.  Returns 1 to retry with a
+// larger candidate list, EPI3_OK, or an error.
+int finish_scan(epi3_handle* h, int top_k, int attempt) {
+    CK(launch_select(h->d_ctrl, h->d_cand, h->cand_cap, top_k, h->k2.rel, h->k2.abs_, h->stream),
+       "select launch");
+    CK(launch_rescore(h->pl, h->k2, h->d_ctrl, h->d_cand, h->cand_cap, h->d_fin, h->sm_count * 8,
+                      h->stream), "rescore launch");
+    CK(launch_final(h->d_ctrl, h->d_fin, top_k, h->d_out_scores, h->d_out_trip, h->stream),
+       "final launch");
+    CK(cudaEventRecord(h->ev[3], h->stream), "event");
+    CK(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream),
+       "read status");
+    if (!(h->flags & EPI3_DEVICE_PTRS)) {
+        CK(cudaMemcpyAsync(h->h_scores, h->d_out_scores, sizeof(double) * top_k,
+                           cudaMemcpyDeviceToHost, h->stream), "read scores");
+        CK(cudaMemcpyAsync(h->h_trip, h->d_out_trip, sizeof(int) * 3 * top_k,
+                           cudaMemcpyDeviceToHost, h->stream), "read triplets");
+    }
+    CK(cudaStreamSynchronize(h->stream), "scan");
+    const int st = h->h_ctrl->status;
+    if (st & kStTimeout)
+        return fail(EPI3_ERR_TIMEOUT, "a bounded device-side wait of the scan ran out");
+    if (st & kStCandOverflow) {
+        if (h->cand_cap >= (1LL << 24) || attempt >= 3)
+            return fail(EPI3_ERR_OVERFLOW, "more than %lld FP32 candidates", h->cand_cap);
+        cudaFree(h->d_cand);
+        h->d_cand = nullptr;
+        h->cand_cap *= 8;
+        CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
+        return 1;
+    }
+    if (st & kStFinalOverflow)
+        return fail(EPI3_ERR_OVERFLOW,
+                    "more than %d triplets lie within the FP32 error band of the k-th best",
+                    kFinalCap);
+    if (st & (kStInternal | kStBadIndex))
+        return fail(EPI3_ERR_CUDA, "internal error in the candidate stage (status %d)", st);
+    return EPI3_OK;
+}
+
+int copy_out(epi3_handle* h, int32_t* out_trip, double* out_scores, int32_t* n_out) {
+    const int nout = (int)h->h_ctrl->n_out;
+    if (h->flags & EPI3_DEVICE_PTRS) {
+        CK(cudaMemcpyAsync(out_scores, h->d_out_scores, sizeof(double) * nout,
+                           cudaMemcpyDeviceToDevice, h->stream), "copy scores");
+        CK(cudaMemcpyAsync(out_trip, h->d_out_trip, sizeof(int) * 3 * nout,
+                           cudaMemcpyDeviceToDevice, h->stream), "copy triplets");
+        CK(cudaStreamSynchronize(h->stream), "copy outputs");
+    } else {
+        memcpy(out_scores, h->h_scores, sizeof(double) * nout);
+        memcpy(out_trip, h->h_trip, sizeof(int) * 3 * nout);
+    }
+    if (n_out) *n_out = nout;
+    return EPI3_OK;
+}
+
+int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long long nt, int top_k,
+                  int32_t* out_trip, double* out_scores, int32_t* n_out) {
+    const bool fp8 = path == EPI3_PATH_MMA;
+    const int grid = h->sm_count;
+    for (int attempt = 0;; ++attempt) {
+        if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
+        CK(cudaEventRecord(h->ev[0], h->stream), "event");
+        CK(launch_reset(h->d_ctrl, h->stream), "reset launch");
+        CK(cudaEventRecord(h->ev[1], h->stream), "event");
+        CK(launch_scan_mma(h->pl, h->k2, h->ptab, h->d_oh, h->oh_off1, h->oh_ks[0], h->oh_ks[1],
+                           h->d_tiles, h->n_tiles, pb, pe, h->d_ctrl, h->d_cand, h->cand_cap, top_k,
+                           fp8, grid, h->stream), "mma scan launch");
+        CK(cudaEventRecord(h->ev[2], h->stream), "event");
+        const int rc = finish_scan(h, top_k, attempt);
+        if (rc == 1) continue;
+        if (rc != EPI3_OK) return rc;
+        break;
+    }
+    const int rc = copy_out(h, out_trip, out_scores, n_out);
+    if (rc != EPI3_OK) return rc;
+    epi3_stats& s = h->stats;
+    s.n_triplets = nt;
+    s.n_candidates = h->h_ctrl->n_cand;
+    s.n_rescored = h->h_ctrl->n_final;
+    s.path = path;
+    s.grid = grid;
+    s.block = 448;
+    s.kernel_launches = 5;
+    s.k2_rel_bound = h->k2.rel;
+    s.k2_abs_bound = h->k2.abs_;
+    cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
+    return EPI3_OK;
+}
+
 int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* out_trip,
               double* out_scores, int32_t* n_out, bool exact_k) {
     if (!h) return fail(EPI3_ERR_ARG, "null handle");
@@ -257,13 +435,24 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     }
     if (n_out) *n_out = 0;
     if (top_k == 0) return EPI3_OK;
-    if (h->path != EPI3_PATH_POPC && h->path != EPI3_PATH_AUTO)
-        return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", h->path);
+    const int path = resolve_path(h);
+    if (path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8 && path != EPI3_PATH_MMA &&
+        path != EPI3_PATH_MMA16)
+        return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
+    const bool mma = path == EPI3_PATH_MMA || path == EPI3_PATH_MMA16;
+    if (path != EPI3_PATH_POPC) {
+        int rc = ensure_pair_tables(h);
+        if (rc == EPI3_OK && mma) rc = ensure_onehot(h, path == EPI3_PATH_MMA);
+        if (rc == EPI3_OK && mma) rc = ensure_tiles(h, pb, pe);
+        if (rc != EPI3_OK) return rc;
+    }
+    if (mma) return scan_mma_impl(h, path, pb, pe, nt, top_k, out_trip, out_scores, n_out);
 
     const int block = h->threads;
-    const size_t smem = scan_popc_smem(h->pl);
+    const size_t smem = path == EPI3_PATH_POPC8 ? scan_popc8_smem(h->pl) : scan_popc_smem(h->pl);
     int occ = 0;
-    CK(scan_popc_occupancy(block, smem, &occ), "scan occupancy");
+    if (path == EPI3_PATH_POPC8) CK(scan_popc8_occupancy(block, smem, &occ), "scan occupancy");
+    else CK(scan_popc_occupancy(block, smem, &occ), "scan occupancy");
     if (occ < 1) return fail(EPI3_ERR_UNSUPPORTED, "scan kernel does not fit (smem %zu)", smem);
     const int per_sm = h->ctas_per_sm > 0 && h->ctas_per_sm < occ ? h->ctas_per_sm : occ;
     const int grid = h->sm_count * per_sm;
@@ -275,6 +464,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         ScanArgs a;
         a.pl = h->pl;
         a.k2 = h->k2;
+        a.pt = h->ptab;
         a.ctrl = h->d_ctrl;
         a.cand = h->d_cand;
         a.cand_cap = h->cand_cap;
@@ -282,7 +472,8 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         a.pair_end = pe;
         a.top_k = top_k;
         CK(cudaEventRecord(h->ev[1], h->stream), "event");
-        CK(launch_scan_popc(a, grid, block, smem, h->stream), "scan launch");
+        if (path == EPI3_PATH_POPC8) CK(launch_scan_popc8(a, grid, block, smem, h->stream), "scan launch");
+        else CK(launch_scan_popc(a, grid, block, smem, h->stream), "scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         CK(launch_select(h->d_ctrl, h->d_cand, h->cand_cap, top_k, h->k2.rel, h->k2.abs_, h->stream),
            "select launch");
@@ -335,7 +526,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     s.n_triplets = nt;
     s.n_candidates = h->h_ctrl->n_cand;
     s.n_rescored = h->h_ctrl->n_final;
-    s.path = EPI3_PATH_POPC;
+    s.path = path;
     s.grid = grid;
     s.block = block;
     s.kernel_launches = 5;
@@ -348,8 +539,12 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
 }
 
 int per_triplet(epi3_handle* h, long long n, const int32_t* trip, int32_t* out_counts,
-                float* out_s32, double* out_s64) {
+                float* out_s32, double* out_s64, int path) {
     if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    if (path == EPI3_PATH_POPC8) {
+        const int rc = ensure_pair_tables(h);
+        if (rc != EPI3_OK) return rc;
+    }
     if (n < 0 || (n > 0 && !trip)) return fail(EPI3_ERR_ARG, "bad triplet list");
     if (n == 0) return EPI3_OK;
     const bool dev = (h->flags & EPI3_DEVICE_PTRS) != 0;
@@ -374,7 +569,7 @@ int per_triplet(epi3_handle* h, long long n, const int32_t* trip, int32_t* out_c
         }
         if ((e = launch_reset(h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "reset"); break; }
         const bool k2 = out_s32 || out_s64;
-        if ((e = launch_tables(h->pl, k2 ? &h->k2 : nullptr, n, d_trip, d_counts, d_s32, d_s64, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "tables launch"); break; }
+        if ((e = launch_tables(h->pl, path == EPI3_PATH_POPC8 ? &h->ptab : nullptr, k2 ? &h->k2 : nullptr, n, d_trip, d_counts, d_s32, d_s64, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "tables launch"); break; }
         if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
         if (!dev) {
             if (out_counts && (e = cudaMemcpyAsync(out_counts, d_counts, sizeof(int) * 54 * n, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read counts"); break; }
@@ -468,17 +663,18 @@ int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_
 int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,
                 int32_t path) {
     g_err.clear();
-    if (path != EPI3_PATH_AUTO && path != EPI3_PATH_POPC)
+    if (path != EPI3_PATH_AUTO && path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8)
         return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
     if (n > 0 && !out_counts) return fail(EPI3_ERR_ARG, "null out_counts");
-    return per_triplet(h, n, triplets, out_counts, nullptr, nullptr);
+    return per_triplet(h, n, triplets, out_counts, nullptr, nullptr,
+                       path == EPI3_PATH_AUTO ? EPI3_PATH_POPC : path);
 }
 
 int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k2_f32,
                 double* out_k2_f64) {
     g_err.clear();
     if (n > 0 && !out_k2_f32 && !out_k2_f64) return fail(EPI3_ERR_ARG, "no output requested");
-    return per_triplet(h, n, triplets, nullptr, out_k2_f32, out_k2_f64);
+    return per_triplet(h, n, triplets, nullptr, out_k2_f32, out_k2_f64, EPI3_PATH_POPC);
 }
 
 int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
@@ -487,6 +683,9 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
     if (!strcmp(key, "path")) {
         if (!strcmp(value, "auto")) h->path = EPI3_PATH_AUTO;
         else if (!strcmp(value, "popc")) h->path = EPI3_PATH_POPC;
+        else if (!strcmp(value, "popc8")) h->path = EPI3_PATH_POPC8;
+        else if (!strcmp(value, "mma")) h->path = EPI3_PATH_MMA;
+        else if (!strcmp(value, "mma16")) h->path = EPI3_PATH_MMA16;
         else return fail(EPI3_ERR_UNSUPPORTED, "path '%s' not available", value);
         return EPI3_OK;
     }

@@ -23,6 +23,7 @@ constexpr int kStCandOverflow = 4;
 constexpr int kStFinalOverflow = 8;
 constexpr int kStInternal = 16;
 constexpr int kStBadIndex = 32;
+constexpr int kStTimeout = 64;
 
 // Device control block of one scan.  Zeroed (then thr set to +inf) before each scan.
 struct Ctrl {
@@ -65,9 +66,20 @@ struct K2Tables {
     float rel, abs_;              // |s32 - s64| <= rel * s + abs_
 };
 
+// Pair tables for the 8-cell forms: for SNPs m1 < m2 (pair index p = m2(m2-1)/2 + m1)
+// and class c, pt[c * n_pairs + p] = {n00, n01, n10, n11}, nab = samples with genotype a at
+// m1 and b at m2; marg[c * M + m] = {n0, n1}; n_c = class sizes.
+struct PairTables {
+    const int4* pt;
+    const int2* marg;
+    long long n_pairs;
+    int n_c[2];
+};
+
 struct ScanArgs {
     Planes pl;
     K2Tables k2;
+    PairTables pt;
     Ctrl* ctrl;
     Cand* cand;
     long long cand_cap;
@@ -89,10 +101,24 @@ cudaError_t launch_rescore(const Planes& pl, const K2Tables& k2, Ctrl* ctrl, con
                            long long cand_cap, Final* fin, int grid, cudaStream_t st);
 cudaError_t launch_final(Ctrl* ctrl, const Final* fin, int top_k, double* out_scores,
                          int* out_trip, cudaStream_t st);
-cudaError_t launch_tables(const Planes& pl, const K2Tables* k2, long long n, const int* trip,
-                          int* out_counts, float* out_s32, double* out_s64, Ctrl* ctrl,
-                          cudaStream_t st);
+cudaError_t launch_tables(const Planes& pl, const PairTables* pt, const K2Tables* k2, long long n,
+                          const int* trip, int* out_counts, float* out_s32, double* out_s64,
+                          Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
+cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long n_pairs,
+                               cudaStream_t st);
+cudaError_t launch_scan_popc8(const ScanArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+size_t scan_popc8_smem(const Planes& pl);
+size_t scan_mma_smem();
+int mma_samples_per_step(bool fp8);
+cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
+                          int kb_count, bool fp8, cudaStream_t st);
+cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTables& pt,
+                            const uint8_t* oh, long long off1, int KS0, int KS1, const int4* tiles,
+                            long long n_tiles, long long pair_begin, long long pair_end, Ctrl* ctrl,
+                            Cand* cand, long long cand_cap, int top_k, bool fp8, int grid,
+                            cudaStream_t st);
+cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 
 // Message returned by epi3_last_error() on this thread.
 void set_last_error(const char* msg);
@@ -120,6 +146,54 @@ __device__ inline void decode_pair(long long p, int* i, int* j) {
     while ((jj + 1) * jj / 2 <= p) ++jj;
     *j = (int)jj;
     *i = (int)(p - jj * (jj - 1) / 2);
+}
+
+__host__ __device__ inline long long pair_index(int m1, int m2) {  // m1 < m2
+    return (long long)m2 * (m2 - 1) / 2 + m1;
+}
+
+// The 27 cells of one class from the 8 cells with every genotype in {0, 1}, by exact
+// integer inclusion-exclusion over the pair tables and single-SNP marginals (a cell with
+// genotype 2 at one SNP is the pair count minus the two cells with 0 and 1 there).
+//   n8[4a + 2b + z] = #(gX = a, gY = b, gZ = z);  pxy = (X, Y) pair table {n00,n01,n10,n11},
+//   pxz = (X, Z), pyz = (Y, Z);  mx, my, mz = {n0, n1};  nc = class size.
+//   r[9 gX + 3 gY + gZ] for gX, gY, gZ in {0, 1, 2}.
+__host__ __device__ __forceinline__ void derive27(const int* n8, int4 pxy, int4 pxz, int4 pyz,
+                                                  int2 mx, int2 my, int2 mz, int nc, int* r) {
+    const int xy[2][2] = {{pxy.x, pxy.y}, {pxy.z, pxy.w}};
+    const int xz[2][2] = {{pxz.x, pxz.y}, {pxz.z, pxz.w}};
+    const int yz[2][2] = {{pyz.x, pyz.y}, {pyz.z, pyz.w}};
+    const int mxa[2] = {mx.x, mx.y}, myb[2] = {my.x, my.y}, mzc[2] = {mz.x, mz.y};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
+            r[9 * a + 3 * b + 0] = c0;
+            r[9 * a + 3 * b + 1] = c1;
+            r[9 * a + 3 * b + 2] = xy[a][b] - c0 - c1;                     // (a, b, 2)
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int z = 0; z < 2; ++z) r[9 * a + 6 + z] = xz[a][z] - r[9 * a + z] - r[9 * a + 3 + z];  // (a,2,z)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int z = 0; z < 2; ++z) r[18 + 3 * b + z] = yz[b][z] - r[3 * b + z] - r[9 + 3 * b + z];  // (2,b,z)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)  // (a, 2, 2): pair (X,Y) count at (a, 2) minus (a,2,0), (a,2,1)
+        r[9 * a + 8] = (mxa[a] - xy[a][0] - xy[a][1]) - r[9 * a + 6] - r[9 * a + 7];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)  // (2, b, 2)
+        r[18 + 3 * b + 2] = (myb[b] - xy[0][b] - xy[1][b]) - r[18 + 3 * b] - r[18 + 3 * b + 1];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)  // (2, 2, z)
+        r[24 + z] = (mzc[z] - xz[0][z] - xz[1][z]) - r[18 + z] - r[21 + z];
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < 26; ++q) s += r[q];
+    r[26] = nc - s;                                                       // (2, 2, 2)
 }
 
 // FP32 K2 (Eq. 1) of a 2 x 27 table.  hi parts are multiples of 2^-g below 2^(24-g):

@@ -1,0 +1,630 @@
+// Tensor-core counting scan: the triplet count as a dense contraction on tcgen05.
+//
+// For a fixed first SNP i and class c the 8 cells with genotypes in {0,1} of every
+// triplet (i, j, k) are one GEMM over the class's samples s:
+//     D[(k, z), (j, a, b)] = sum_s [g_k(s) = z] * ([g_i(s) = a] & [g_j(s) = b]),
+// A = one-hot rows of the third SNP (2 rows per SNP), B = one-hot pair products (4 rows
+// per second SNP), both 0/1 values, FP32 accumulation in TMEM (counts < 2^24: exact).
+// The other 19 cells follow exactly from pair tables and marginals (derive27), then K2
+// and the candidate band exactly as in the POPC scan.  (The paper's kernels use POPCNT,
+// Sec. IV; its related work, Sec. II, points at tensor-core formulations.)
+//
+// Tile = (i, 64 third SNPs, 32 second SNPs): MMA M = 128 rows (k, z), N = 128 columns
+// (j, a, b), K = 128 samples (FP8 E4M3 operands) or 64 samples (FP16) per stage, four
+// tcgen05.mma per stage.  Both classes accumulate into separate 128-column TMEM regions;
+// two accumulator buffers (512 columns) let the epilogue of one tile overlap the MMAs of
+// the next.  A is pre-tiled in HBM in the exact 128B-swizzled shared-memory image and
+// fetched with one cp.async.bulk per stage; B is expanded from the bit planes by four
+// producer warps straight into the swizzled layout.
+//
+// Warp roles (14 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
+// (two warps per TMEM lane quadrant), 10..13 = B producers.  Every mbarrier wait is
+// bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
+// frees TMEM and returns.
+#include "epi3_internal.cuh"
+
+namespace epi3 {
+
+namespace {
+
+constexpr int kKB = 64;                  // third SNPs per tile (A rows = 2 per SNP)
+constexpr int kJB = 32;                  // second SNPs per tile (B rows = 4 per SNP)
+constexpr int kStages = 4;
+constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
+constexpr int kThreads = 448;
+constexpr int kWarpMma = 1;
+constexpr int kEpiWarp0 = 2, kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
+constexpr int kProdWarp0 = 10, kProdThreads = 128;
+constexpr int kTmemCols = 512;
+constexpr int kPrefetch = 4;             // producer prefetch distance (stages)
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
+constexpr int kCandCapMma = 1024;
+constexpr int kRoundMax = 2 * kEpiThreads;   // appends per epilogue round at most
+constexpr int kStTimeoutBit = 64;
+
+struct MmaArgs {
+    Planes pl;
+    K2Tables k2;
+    PairTables pt;
+    const uint8_t* oh;       // pre-tiled A chunks
+    long long oh_off[2];     // chunk index of (class c, k-block 0, step 0)
+    int KS[2];               // K-steps per class
+    const int4* tiles;       // (i, jb, kb, 0)
+    long long n_tiles;
+    long long pair_begin, pair_end;   // pairs (i, j) scanned: p = j(j-1)/2 + i in [begin, end)
+    Ctrl* ctrl;
+    Cand* cand;
+    long long cand_cap;
+    int top_k;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of the given parity; false on timeout (1 s) or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, unsigned parity, volatile int* abort_flag) {
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if ((it & 63u) == 0u) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
+    }
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t a, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned bytes,
+                                         uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(mbar) : "memory");
+}
+template <bool kFp8>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+    if (kFp8) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+    }
+}
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void epi_bar() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128B swizzle, rows of 128 bytes,
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, A/B E4M3 (kind::f8f6f4) or F16 (kind::f16),
+// both K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Byte offset of 16-byte unit u of row r in a 128-row, 128 B-per-row 128B-swizzled tile.
+__host__ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t u) {
+    return (r >> 3) * 1024u + (r & 7u) * 128u + ((u ^ (r & 7u)) << 4);
+}
+
+// 4 bits -> 4 bytes of value `one` (E4M3 1.0 = 0x38) or 0.
+__device__ __forceinline__ uint32_t nib_to_bytes(uint32_t nib, uint32_t one) {
+    return ((nib * 0x00204081u) & 0x01010101u) * one;
+}
+// 2 bits -> 2 FP16 values (1.0 = 0x3C00) packed in one word.
+__device__ __forceinline__ uint32_t bits2_to_h2(uint32_t b2) {
+    return ((b2 * 0x8001u) & 0x10001u) * 0x3C00u;
+}
+
+// Expand the 128 bytes of one operand row from its sample bits into the swizzled tile.
+// FP8: 128 samples = 4 words; FP16: 64 samples = 2 words (w[0], w[1]).
+template <bool kFp8>
+__device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint32_t* w) {
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+        uint4 v;
+        if (kFp8) {  // unit u = samples 16u .. 16u+15 = half (u & 1) of word u >> 1
+            const uint32_t h = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
+            v.x = nib_to_bytes(h & 0xF, 0x38u);
+            v.y = nib_to_bytes((h >> 4) & 0xF, 0x38u);
+            v.z = nib_to_bytes((h >> 8) & 0xF, 0x38u);
+            v.w = nib_to_bytes(h >> 12, 0x38u);
+        } else {  // unit u = samples 8u .. 8u+7 = byte (u & 3) of word u >> 2
+            const uint32_t b = (w[u >> 2] >> ((u & 3) * 8)) & 0xFFu;
+            v.x = bits2_to_h2(b & 3);
+            v.y = bits2_to_h2((b >> 2) & 3);
+            v.z = bits2_to_h2((b >> 4) & 3);
+            v.w = bits2_to_h2(b >> 6);
+        }
+        *reinterpret_cast<uint4*>(tile + sw128_off(r, u)) = v;
+    }
+}
+
+// Words of K-step ks of class c, plane p, SNP m (zero words past the class or for m >= M).
+template <bool kFp8>
+__device__ __forceinline__ uint4 step_bits(const Planes& pl, int c, int p, int m, int ks) {
+    if (m >= pl.M) return make_uint4(0, 0, 0, 0);
+    const int w4 = kFp8 ? ks : (ks >> 1);
+    const uint4 g = __ldg(pl.planes + pl.coff[c] + ((size_t)p * pl.W4[c] + w4) * pl.M + m);
+    if (kFp8) return g;
+    return (ks & 1) ? make_uint4(g.z, g.w, 0, 0) : make_uint4(g.x, g.y, 0, 0);
+}
+
+__device__ void sort_cands_epi(Cand* buf, int tid) {
+    for (int size = 2; size <= kCandCapMma; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < kCandCapMma / 2; t += kEpiThreads) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const Cand x = buf[lo], y = buf[hi];
+                if ((x.s > y.s) == up) {
+                    buf[lo] = y;
+                    buf[hi] = x;
+                }
+            }
+            epi_bar();
+        }
+}
+
+struct EpiShared {
+    Cand buf[kCandCapMma];
+    int cnt, keep, stop;
+    float tloc;
+};
+
+// Sort the buffer, publish this CTA's band threshold, keep the entries inside the band;
+// spill to the global list when too many tie.  Called by all epilogue threads.
+__device__ int epi_prune(const MmaArgs& a, EpiShared& es, int cnt, int tid, bool final_flush) {
+    const float kInf = __int_as_float(0x7f800000);
+    if (cnt >= a.top_k) {
+        for (int idx = cnt + tid; idx < kCandCapMma; idx += kEpiThreads) es.buf[idx].s = kInf;
+        epi_bar();
+        sort_cands_epi(es.buf, tid);
+        if (tid == 0) {
+            const float tl = band_threshold(es.buf[a.top_k - 1].s, a.k2.rel, a.k2.abs_);
+            atomicMin(&a.ctrl->thr, __float_as_uint(tl));
+            es.tloc = fminf(es.tloc, tl);
+        }
+    }
+    if (tid == 0) es.keep = 0;
+    epi_bar();
+    const float t = fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr));
+    if (final_flush || cnt < a.top_k) {
+        for (int idx = tid; idx < cnt; idx += kEpiThreads) {
+            const Cand e = es.buf[idx];
+            if (e.s <= t) {
+                const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
+                if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
+                else atomicOr(&a.ctrl->status, kStCandOverflow);
+            }
+        }
+        epi_bar();
+        return 0;
+    }
+    int keep = 0;
+    for (int idx = tid; idx < cnt; idx += kEpiThreads) keep += (es.buf[idx].s <= t);
+    if (keep) atomicAdd(&es.keep, keep);
+    epi_bar();
+    int kept = es.keep;
+    if (kept > kCandCapMma - kRoundMax) {
+        for (int idx = tid; idx < kept; idx += kEpiThreads) {
+            const Cand e = es.buf[idx];
+            const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
+            if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
+            else atomicOr(&a.ctrl->status, kStCandOverflow);
+        }
+        kept = 0;
+    }
+    epi_bar();
+    return kept;
+}
+
+template <bool kFp8>
+__global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
+    uint8_t* base = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = base;
+    uint8_t* sB = base + kStages * kChunk;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * kStages * kChunk);
+    // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], acc_empty[2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    EpiShared& es = *reinterpret_cast<EpiShared*>(base + 2 * kStages * kChunk + 256);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t fullA0 = smem_u32(bars), fullB0 = smem_u32(bars + kStages),
+                   empty0 = smem_u32(bars + 2 * kStages), accF0 = smem_u32(bars + 3 * kStages),
+                   accE0 = smem_u32(bars + 3 * kStages + 2);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(fullA0 + 8 * s, 1);
+            mbar_init(fullB0 + 8 * s, kProdThreads);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accF0 + 8 * b, 1);
+            mbar_init(accE0 + 8 * b, kEpiWarps);
+        }
+        *abort_flag = 0;
+        es.cnt = 0;
+        es.stop = 0;
+        es.tloc = __int_as_float(0x7f800000);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int steps_per_tile = a.KS[0] + a.KS[1];
+    const long long my_tiles =
+        a.n_tiles > blockIdx.x ? (a.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long n_steps = my_tiles * steps_per_tile;
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(&a.ctrl->status, kStTimeoutBit);
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------ A loader (lane 0)
+        if (lane == 0) {
+            long long q = 0;
+            for (; q < n_steps; ++q) {
+                const int s = (int)(q % kStages);
+                const unsigned ph = (unsigned)((q / kStages) & 1);
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
+                    fail();
+                    break;
+                }
+                const long long tl = q / steps_per_tile;
+                const int r = (int)(q - tl * steps_per_tile);
+                const int c = r < a.KS[0] ? 0 : 1;
+                const int ks = c ? r - a.KS[0] : r;
+                const int4 tile = a.tiles[blockIdx.x + tl * gridDim.x];
+                const long long chunk = a.oh_off[c] + (long long)tile.z * a.KS[c] + ks;
+                mbar_arrive_tx(fullA0 + 8 * s, kChunk);
+                bulk_g2s(smem_u32(sA + s * kChunk), a.oh + chunk * kChunk, kChunk, fullA0 + 8 * s);
+            }
+            // drain: the copies of the last stages issued must land before the CTA exits
+            for (long long d = (q > kStages ? q - kStages : 0); d < q; ++d) {
+                const int s = (int)(d % kStages);
+                mbar_wait(fullA0 + 8 * s, (unsigned)((d / kStages) & 1), abort_flag);
+            }
+        }
+    } else if (warp == kWarpMma) {
+        // ------------------------------------------------ MMA issuer (lane 0)
+        if (lane == 0) {
+            long long q = 0;
+            bool ok = true;
+            for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+                const int buf = (int)(tl & 1);
+                if (!mbar_wait(accE0 + 8 * buf, (unsigned)(((tl >> 1) & 1) ^ 1), abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                for (int c = 0; c < 2 && ok; ++c) {
+                    const uint32_t d = tmem + buf * 256 + c * 128;
+                    for (int ks = 0; ks < a.KS[c]; ++ks, ++q) {
+                        const int s = (int)(q % kStages);
+                        const unsigned ph = (unsigned)((q / kStages) & 1);
+                        if (!mbar_wait(fullA0 + 8 * s, ph, abort_flag) ||
+                            !mbar_wait(fullB0 + 8 * s, ph, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t da = sw128_desc(smem_u32(sA + s * kChunk));
+                        const uint64_t db = sw128_desc(smem_u32(sB + s * kChunk));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
+                            tc_mma<kFp8>(d, da + 2 * kk, db + 2 * kk, kIdesc,
+                                         (ks > 0 || kk > 0) ? 1u : 0u);
+                        tc_commit(empty0 + 8 * s);
+                    }
+                }
+                if (ok) tc_commit(accF0 + 8 * buf);
+            }
+        }
+    } else if (warp >= kProdWarp0) {
+        // ------------------------------------------------ B producers: row r = (jj, a, b)
+        const int r = threadIdx.x - kProdWarp0 * 32;
+        const int jj = r >> 2, ga = (r >> 1) & 1, gb = r & 1;
+        uint4 rx[kPrefetch], ry[kPrefetch];
+        auto fetch = [&](long long q, uint4& x, uint4& y) {
+            if (q >= n_steps) return;
+            const long long tl = q / steps_per_tile;
+            const int rr = (int)(q - tl * steps_per_tile);
+            const int c = rr < a.KS[0] ? 0 : 1;
+            const int ks = c ? rr - a.KS[0] : rr;
+            const int4 tile = a.tiles[blockIdx.x + tl * gridDim.x];
+            x = step_bits<kFp8>(a.pl, c, ga, tile.x, ks);
+            y = step_bits<kFp8>(a.pl, c, gb, tile.y * kJB + jj, ks);
+        };
+#pragma unroll
+        for (int u = 0; u < kPrefetch; ++u) fetch(u, rx[u], ry[u]);
+        bool ok = true;
+        for (long long q0 = 0; q0 < n_steps && ok; q0 += kPrefetch) {
+#pragma unroll
+            for (int u = 0; u < kPrefetch; ++u) {
+                const long long q = q0 + u;
+                if (q >= n_steps || !ok) break;
+                const int s = (int)(q % kStages);
+                const unsigned ph = (unsigned)((q / kStages) & 1);
+                const uint32_t w[4] = {rx[u].x & ry[u].x, rx[u].y & ry[u].y, rx[u].z & ry[u].z,
+                                       rx[u].w & ry[u].w};
+                fetch(q + kPrefetch, rx[u], ry[u]);
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                store_row<kFp8>(sB + s * kChunk, (uint32_t)r, w);
+                fence_proxy_async();
+                mbar_arrive(fullB0 + 8 * s);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..9)
+        const int tid = threadIdx.x - kEpiWarp0 * 32;   // 0..255
+        const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;
+        const int L = quad * 32 + lane;                 // TMEM lane = A row = (kk, z)
+        const int kk = L >> 1, z = L & 1;
+        const int M = a.pl.M;
+        int cnt = 0;
+        bool ok = true;
+        for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+            const int buf = (int)(tl & 1);
+            const int4 tile = a.tiles[blockIdx.x + tl * gridDim.x];
+            const int i = tile.x, j0 = tile.y * kJB, k = tile.z * kKB + kk;
+            if (!mbar_wait(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag)) fail();
+            epi_bar();  // uniform decision: every epilogue thread stops on the same tile
+            if (tid == 0) es.stop = *abort_flag;
+            epi_bar();
+            if (es.stop) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const bool krow = (k < M) && (k > i);
+            int4 pxz[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+            int2 mz[2] = {make_int2(0, 0), make_int2(0, 0)}, mx[2];
+            if (krow) {
+                pxz[0] = __ldg(a.pt.pt + pair_index(i, k));
+                pxz[1] = __ldg(a.pt.pt + a.pt.n_pairs + pair_index(i, k));
+                mz[0] = __ldg(a.pt.marg + k);
+                mz[1] = __ldg(a.pt.marg + M + k);
+            }
+            mx[0] = __ldg(a.pt.marg + i);
+            mx[1] = __ldg(a.pt.marg + M + i);
+            for (int gi = 0; gi < 4; ++gi) {
+                const int g = half + 2 * gi;            // 16-column group = 4 second SNPs
+                uint32_t v[2][16];
+                const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                    tc_ld16(tmem + lane_base + buf * 256 + c * 128 + 16 * g, v[c]);
+                tc_wait_ld();
+                int cv[2][16];
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int t = 0; t < 16; ++t)
+                        cv[c][t] = a.KS[c] ? __float2int_rn(__uint_as_float(v[c][t])) : 0;
+                // my triplets: jj = 4g + z + 2m; the partner lane (other z) holds the
+                // other third-SNP genotype of the same (k, jj): swap what each one needs.
+                int got[2][8];
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+#pragma unroll
+                        for (int ab = 0; ab < 4; ++ab)
+                            got[c][4 * m + ab] = __shfl_xor_sync(
+                                0xffffffffu, cv[c][((1 - z) + 2 * m) * 4 + ab], 1);
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int jj = 4 * g + z + 2 * m;
+                    const int j = j0 + jj;
+                    if (!(krow && j > i && j < k)) continue;
+                    const long long pij = pair_index(i, j);
+                    if (pij < a.pair_begin || pij >= a.pair_end) continue;
+                    int r0[kCells], r1[kCells];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        int n8[8];
+#pragma unroll
+                        for (int ab = 0; ab < 4; ++ab) {
+                            const int mine = cv[c][(z + 2 * m) * 4 + ab];
+                            const int other = got[c][4 * m + ab];
+                            n8[2 * ab + z] = mine;       // n8[4a + 2b + gz], ab = 2a + b
+                            n8[2 * ab + (1 - z)] = other;
+                        }
+                        derive27(n8, __ldg(a.pt.pt + c * a.pt.n_pairs + pair_index(i, j)), pxz[c],
+                                 __ldg(a.pt.pt + c * a.pt.n_pairs + pair_index(j, k)), mx[c],
+                                 __ldg(a.pt.marg + (size_t)c * M + j), mz[c], a.pt.n_c[c],
+                                 c ? r1 : r0);
+                    }
+                    const float s = k2_f32(r0, r1, a.k2.lf2);
+                    if (s <= fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr))) {
+                        const int idx = atomicAdd(&es.cnt, 1);
+                        es.buf[idx] = Cand{s, i, j, k};
+                    }
+                }
+                epi_bar();
+                cnt = es.cnt;
+                epi_bar();
+                if (cnt > kCandCapMma - kRoundMax) {
+                    cnt = epi_prune(a, es, cnt, tid, false);
+                    if (tid == 0) es.cnt = cnt;
+                    epi_bar();
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(accE0 + 8 * buf);
+        }
+        epi_prune(a, es, cnt, tid, true);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols) : "memory");
+    }
+}
+
+// Pre-tiled one-hot A chunks: chunk (c, kb, ks) holds rows r = 2 kk + z (third SNP
+// 64 kb + kk, genotype z) over the K-step's samples, already in the swizzled image.
+template <bool kFp8>
+__global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off1, int KS0, int KS1,
+                              int kb_count) {
+    const long long total = ((long long)kb_count * (KS0 + KS1)) * 128;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(t & 127);
+        const long long ch = t >> 7;  // chunk, in (class, kb, ks) order
+        int c, kb, ks;
+        if (ch < (long long)kb_count * KS0) {
+            c = 0;
+            kb = (int)(ch / KS0);
+            ks = (int)(ch % KS0);
+        } else {
+            const long long q = ch - (long long)kb_count * KS0;
+            c = 1;
+            kb = (int)(q / KS1);
+            ks = (int)(q % KS1);
+        }
+        const int m = kb * kKB + (r >> 1), p = r & 1;
+        const uint4 g = step_bits<kFp8>(pl, c, p, m, ks);
+        const uint32_t w[4] = {g.x, g.y, g.z, g.w};
+        uint8_t* tile = oh + (c ? off1 + (long long)kb * KS1 + ks : (long long)kb * KS0 + ks) * kChunk;
+        store_row<kFp8>(tile, (uint32_t)r, w);
+    }
+}
+
+}  // namespace
+
+size_t scan_mma_smem() {
+    return 1024 + 2 * kStages * kChunk + 256 + sizeof(EpiShared) + 64;
+}
+
+int mma_samples_per_step(bool fp8) { return fp8 ? 128 : 64; }
+
+cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
+                          int kb_count, bool fp8, cudaStream_t st) {
+    const long long total = ((long long)kb_count * (KS0 + KS1)) * 128;
+    const int blocks = (int)((total + 255) / 256 < 65535 * 8 ? (total + 255) / 256 : 65535 * 8);
+    if (total == 0) return cudaSuccess;
+    if (fp8) onehot_kernel<true><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
+    else onehot_kernel<false><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTables& pt,
+                            const uint8_t* oh, long long off1, int KS0, int KS1, const int4* tiles,
+                            long long n_tiles, long long pair_begin, long long pair_end, Ctrl* ctrl,
+                            Cand* cand, long long cand_cap, int top_k, bool fp8, int grid,
+                            cudaStream_t st) {
+    MmaArgs a;
+    a.pl = pl;
+    a.k2 = k2;
+    a.pt = pt;
+    a.oh = oh;
+    a.oh_off[0] = 0;
+    a.oh_off[1] = off1;
+    a.KS[0] = KS0;
+    a.KS[1] = KS1;
+    a.tiles = tiles;
+    a.n_tiles = n_tiles;
+    a.pair_begin = pair_begin;
+    a.pair_end = pair_end;
+    a.ctrl = ctrl;
+    a.cand = cand;
+    a.cand_cap = cand_cap;
+    a.top_k = top_k;
+    const size_t smem = scan_mma_smem();
+    cudaError_t e;
+    if (fp8) {
+        e = cudaFuncSetAttribute(scan_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        scan_mma_kernel<true><<<grid, kThreads, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(scan_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        scan_mma_kernel<false><<<grid, kThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace epi3

@@ -1,5 +1,5 @@
-// 27-cell counting scan: LOP3 AND + POPC over bit planes, fused FP32 K2 and candidate
-// selection (Sec. III, Alg. 2, Sec. IV-B).
+// Counting scans: LOP3 AND + POPC over bit planes, fused FP32 K2 and candidate selection
+// (Sec. III, Alg. 2, Sec. IV-B), in the paper's 27-cell form and in an 8-cell form.
 //
 // Work decomposition (GB300 design, not the paper's thread grid): a persistent grid of
 // CTAs pulls SNP pairs (i, j) from a global counter, heaviest pairs first (pair index
@@ -79,6 +79,45 @@ __device__ __forceinline__ void count_class(const Planes& pl, int c, int k, cons
     r[kCells - 1] -= pl.pad[c];
 }
 
+// 8-cell form: pair products X[a] & Y[b] for a, b in {0, 1} only: sxy[(2a + b) * W4 + w4].
+__device__ __forceinline__ void stage_pair8(const Planes& pl, int c, int i, int j, uint4* sxy) {
+    const int W4 = pl.W4[c];
+    const uint4* base = pl.planes + pl.coff[c];
+    const size_t pstride = (size_t)W4 * pl.M;
+    for (int w4 = threadIdx.x; w4 < W4; w4 += blockDim.x) {
+        const size_t o = (size_t)w4 * pl.M;
+        const uint4 x0 = __ldg(base + o + i), x1 = __ldg(base + pstride + o + i);
+        const uint4 y0 = __ldg(base + o + j), y1 = __ldg(base + pstride + o + j);
+        sxy[0 * W4 + w4] = and4(x0, y0);
+        sxy[1 * W4 + w4] = and4(x0, y1);
+        sxy[2 * W4 + w4] = and4(x1, y0);
+        sxy[3 * W4 + w4] = and4(x1, y1);
+    }
+}
+
+// 8 counts n8[4a + 2b + z] of class c for third SNP k (genotypes 0 and 1 only; no pad
+// correction: pad bits are 0 in planes 0 and 1).
+__device__ __forceinline__ void count_class8(const Planes& pl, int c, int k, const uint4* sxy,
+                                             int* n8) {
+    const int W4 = pl.W4[c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) n8[q] = 0;
+    const uint4* z0p = pl.planes + pl.coff[c] + k;
+    const uint4* z1p = z0p + (size_t)W4 * pl.M;
+    const size_t M = (size_t)pl.M;
+#pragma unroll 2
+    for (int w4 = 0; w4 < W4; ++w4) {
+        const uint4 z0 = __ldg(z0p + (size_t)w4 * M);
+        const uint4 z1 = __ldg(z1p + (size_t)w4 * M);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const uint4 v = sxy[g * W4 + w4];
+            n8[2 * g + 0] += popc4(v, z0);
+            n8[2 * g + 1] += popc4(v, z1);
+        }
+    }
+}
+
 // Ascending bitonic sort of the kCtaCand shared candidates by FP32 score.
 __device__ void sort_cands(Cand* buf) {
     for (int size = 2; size <= kCtaCand; size <<= 1) {
@@ -109,9 +148,14 @@ __device__ void flush_cands(const ScanArgs& a, const Cand* buf, int n, float t) 
     }
 }
 
+// kEight = false: the paper's 27-cell count (Alg. 2 with the pair products staged);
+// kEight = true: the 8 cells with genotypes in {0,1} counted, the other 19 derived exactly
+// from the pair tables (derive27).
+template <bool kEight>
 __global__ void __launch_bounds__(256)
-scan_popc27_kernel(const ScanArgs a) {
-    extern __shared__ uint4 sxy[];  // [class][9][W4[class]]
+scan_popc_kernel(const ScanArgs a) {
+    constexpr int kProd = kEight ? 4 : 9;
+    extern __shared__ uint4 sxy[];  // [class][kProd][W4[class]]
     __shared__ Cand cbuf[kCtaCand];
     __shared__ int s_cnt, s_keep;
     __shared__ float s_tloc, s_tglob;
@@ -119,7 +163,9 @@ scan_popc27_kernel(const ScanArgs a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int M = a.pl.M;
     uint4* sxy0 = sxy;
-    uint4* sxy1 = sxy + 9 * a.pl.W4[0];
+    uint4* sxy1 = sxy + kProd * a.pl.W4[0];
+    __shared__ int4 s_pxy[2];
+    __shared__ int2 s_mx[2], s_my[2];
     const float kInf = __int_as_float(0x7f800000);
     if (tid == 0) {
         s_cnt = 0;
@@ -137,16 +183,38 @@ scan_popc27_kernel(const ScanArgs a) {
         if (p >= a.pair_end) break;
         int i, j;
         decode_pair(p, &i, &j);
-        stage_pair(a.pl, 0, i, j, sxy0);
-        stage_pair(a.pl, 1, i, j, sxy1);
+        if (kEight) {
+            stage_pair8(a.pl, 0, i, j, sxy0);
+            stage_pair8(a.pl, 1, i, j, sxy1);
+            if (tid < 2) {
+                s_pxy[tid] = __ldg(a.pt.pt + tid * a.pt.n_pairs + pair_index(i, j));
+                s_mx[tid] = __ldg(a.pt.marg + (size_t)tid * M + i);
+                s_my[tid] = __ldg(a.pt.marg + (size_t)tid * M + j);
+            }
+        } else {
+            stage_pair(a.pl, 0, i, j, sxy0);
+            stage_pair(a.pl, 1, i, j, sxy1);
+        }
         __syncthreads();
         for (int kb = j + 1; kb < M; kb += nt) {
             const int k = kb + tid;
             bool app = false;
             if (k < M) {
                 int r0[kCells], r1[kCells];
-                count_class(a.pl, 0, k, sxy0, r0);
-                count_class(a.pl, 1, k, sxy1, r1);
+                if (kEight) {
+                    int n8[8];
+                    count_class8(a.pl, 0, k, sxy0, n8);
+                    derive27(n8, s_pxy[0], __ldg(a.pt.pt + pair_index(i, k)),
+                             __ldg(a.pt.pt + pair_index(j, k)), s_mx[0], s_my[0],
+                             __ldg(a.pt.marg + k), a.pt.n_c[0], r0);
+                    count_class8(a.pl, 1, k, sxy1, n8);
+                    derive27(n8, s_pxy[1], __ldg(a.pt.pt + a.pt.n_pairs + pair_index(i, k)),
+                             __ldg(a.pt.pt + a.pt.n_pairs + pair_index(j, k)), s_mx[1], s_my[1],
+                             __ldg(a.pt.marg + M + k), a.pt.n_c[1], r1);
+                } else {
+                    count_class(a.pl, 0, k, sxy0, r0);
+                    count_class(a.pl, 1, k, sxy1, r1);
+                }
                 const float s = k2_f32(r0, r1, a.k2.lf2);
                 if (s <= fminf(s_tloc, s_tglob)) {
                     const int idx = atomicAdd(&s_cnt, 1);
@@ -206,17 +274,36 @@ size_t scan_popc_smem(const Planes& pl) {
     return (size_t)9 * (pl.W4[0] + pl.W4[1]) * sizeof(uint4);
 }
 
-cudaError_t scan_popc_occupancy(int block, size_t smem, int* ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(scan_popc27_kernel,
+size_t scan_popc8_smem(const Planes& pl) {
+    return (size_t)4 * (pl.W4[0] + pl.W4[1]) * sizeof(uint4);
+}
+
+template <bool kEight>
+static cudaError_t occupancy(int block, size_t smem, int* ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<kEight>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, scan_popc27_kernel, block,
-                                                         smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, scan_popc_kernel<kEight>,
+                                                         block, smem);
+}
+
+cudaError_t scan_popc_occupancy(int block, size_t smem, int* ctas_per_sm) {
+    return occupancy<false>(block, smem, ctas_per_sm);
+}
+
+cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm) {
+    return occupancy<true>(block, smem, ctas_per_sm);
 }
 
 cudaError_t launch_scan_popc(const ScanArgs& a, int grid, int block, size_t smem,
                              cudaStream_t st) {
-    scan_popc27_kernel<<<grid, block, smem, st>>>(a);
+    scan_popc_kernel<false><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_popc8(const ScanArgs& a, int grid, int block, size_t smem,
+                              cudaStream_t st) {
+    scan_popc_kernel<true><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,50 @@ __device__ void warp_table(const Planes& pl, int x, int y, int z, int* r0, int* 
     }
 }
 
+// 8-cell form of warp_table: counts the cells with genotypes in {0,1} and derives the
+// other 19 from the pair tables (derive27).
+__device__ void warp_table8(const Planes& pl, const PairTables& pt, int x, int y, int z, int* r0,
+                            int* r1) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        int n8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) n8[q] = 0;
+        const int W4 = pl.W4[c];
+        const uint4* base = pl.planes + pl.coff[c];
+        const size_t ps = (size_t)W4 * pl.M;
+        for (int w4 = lane; w4 < W4; w4 += 32) {
+            const size_t o = (size_t)w4 * pl.M;
+            const uint4 X[2] = {__ldg(base + o + x), __ldg(base + ps + o + x)};
+            const uint4 Y[2] = {__ldg(base + o + y), __ldg(base + ps + o + y)};
+            const uint4 Z[2] = {__ldg(base + o + z), __ldg(base + ps + o + z)};
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) n8[4 * a + 2 * b + g] += popc4(X[a], Y[b], Z[g]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int v = n8[q];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            n8[q] = v;
+        }
+        // pair tables are stored for ordered pairs m1 < m2; swap roles when needed
+        auto pair = [&](int u, int v) -> int4 {
+            if (u < v) return __ldg(pt.pt + c * pt.n_pairs + pair_index(u, v));
+            const int4 t = __ldg(pt.pt + c * pt.n_pairs + pair_index(v, u));
+            return make_int4(t.x, t.z, t.y, t.w);  // transpose the 2 x 2 table
+        };
+        derive27(n8, pair(x, y), pair(x, z), pair(y, z), __ldg(pt.marg + (size_t)c * pl.M + x),
+                 __ldg(pt.marg + (size_t)c * pl.M + y), __ldg(pt.marg + (size_t)c * pl.M + z),
+                 pt.n_c[c], c ? r1 : r0);
+    }
+}
+
 __global__ void reset_kernel(Ctrl* ctrl) {
     Ctrl z = {};
     z.thr = 0x7f800000u;
@@ -185,7 +229,7 @@ final_kernel(Ctrl* ctrl, const Final* __restrict__ fin, int top_k, double* out_s
 }
 
 __global__ void __launch_bounds__(256)
-tables_kernel(Planes pl, K2Tables k2, int use_k2, long long n, const int* __restrict__ trip,
+tables_kernel(Planes pl, PairTables ptab, K2Tables k2, int use_k2, long long n, const int* __restrict__ trip,
               int* __restrict__ out_counts, float* __restrict__ out_s32, double* __restrict__ out_s64,
               Ctrl* ctrl) {
     const int lane = threadIdx.x & 31;
@@ -193,12 +237,14 @@ tables_kernel(Planes pl, K2Tables k2, int use_k2, long long n, const int* __rest
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long t = warp; t < n; t += nwarps) {
         const int x = trip[3 * t], y = trip[3 * t + 1], z = trip[3 * t + 2];
-        if (x < 0 || y < 0 || z < 0 || x >= pl.M || y >= pl.M || z >= pl.M) {
+        if (x < 0 || y < 0 || z < 0 || x >= pl.M || y >= pl.M || z >= pl.M ||
+            (ptab.pt && (x == y || y == z || x == z))) {
             if (lane == 0) atomicOr(&ctrl->status, kStBadIndex);
             continue;
         }
         int r0[kCells], r1[kCells];
-        warp_table(pl, x, y, z, r0, r1);
+        if (ptab.pt) warp_table8(pl, ptab, x, y, z, r0, r1);
+        else warp_table(pl, x, y, z, r0, r1);
         if (out_counts && lane < kCells) {
             int v0 = 0, v1 = 0;
 #pragma unroll
@@ -246,15 +292,16 @@ cudaError_t launch_final(Ctrl* ctrl, const Final* fin, int top_k, double* out_sc
     return cudaGetLastError();
 }
 
-cudaError_t launch_tables(const Planes& pl, const K2Tables* k2, long long n, const int* trip,
-                          int* out_counts, float* out_s32, double* out_s64, Ctrl* ctrl,
-                          cudaStream_t st) {
+cudaError_t launch_tables(const Planes& pl, const PairTables* pt, const K2Tables* k2, long long n,
+                          const int* trip, int* out_counts, float* out_s32, double* out_s64,
+                          Ctrl* ctrl, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 7) / 8;  // 8 warps per block
     if (blocks > 65536) blocks = 65536;
     K2Tables kt = k2 ? *k2 : K2Tables{};
-    tables_kernel<<<(int)blocks, 256, 0, st>>>(pl, kt, k2 ? 1 : 0, n, trip, out_counts, out_s32,
-                                               out_s64, ctrl);
+    PairTables ptt = pt ? *pt : PairTables{};
+    tables_kernel<<<(int)blocks, 256, 0, st>>>(pl, ptt, kt, k2 ? 1 : 0, n, trip, out_counts,
+                                               out_s32, out_s64, ctrl);
     return cudaGetLastError();
 }
 

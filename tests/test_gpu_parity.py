@@ -44,7 +44,16 @@ def check_scores(h, g, ph, trip):
     assert np.all(np.abs(s32 - ref) <= bound)
 
 
-def check_scan(h, g, ph, k):
+PATHS = ["popc", "popc8"]
+
+
+def check_scan(h, g, ph, k, paths=PATHS):
+    for path in paths:
+        h.set_option("path", path)
+        _check_scan(h, g, ph, k)
+
+
+def _check_scan(h, g, ph, k):
     tr, sc = h.scan(k)
     otr, osc, _ = oracle.scan_topk(g, ph, k)
     assert np.array_equal(tr, otr), (tr[:5], otr[:5])
@@ -56,7 +65,9 @@ def test_tiny_config_full_parity():
     with epi.Handle(d.genotypes, d.phenotype) as h:
         assert h.shape() == (64, 512, 256, 256)
         trip = all_trip(64)
-        assert np.array_equal(h.tables(trip), oracle.tables(d.genotypes, d.phenotype, trip))
+        ref = oracle.tables(d.genotypes, d.phenotype, trip)
+        assert np.array_equal(h.tables(trip), ref)
+        assert np.array_equal(h.tables(trip, epi.PATH_POPC8), ref)
         check_scores(h, d.genotypes, d.phenotype, trip)
         check_scan(h, d.genotypes, d.phenotype, 10)
         st = h.stats()
@@ -70,7 +81,9 @@ def test_ragged_shapes(m, n, n1):
     g, ph = pins.tiny_data(m, n, n1, seed=100 + m + n)
     with epi.Handle(g, ph) as h:
         trip = all_trip(m)
-        assert np.array_equal(h.tables(trip), pins.numpy_tables(g, ph, trip).astype(np.int32))
+        ref = pins.numpy_tables(g, ph, trip).astype(np.int32)
+        assert np.array_equal(h.tables(trip), ref)
+        assert np.array_equal(h.tables(trip, epi.PATH_POPC8), ref)
         check_scores(h, g, ph, trip)
         check_scan(h, g, ph, min(10, len(trip)))
 
@@ -87,7 +100,9 @@ def test_out_of_order_triplets_take_roles():
     g, ph = pins.tiny_data(9, 200, 90, seed=8)
     with epi.Handle(g, ph) as h:
         trip = all_trip(9)[:, [2, 0, 1]]
-        assert np.array_equal(h.tables(trip), oracle.tables(g, ph, trip))
+        ref = oracle.tables(g, ph, trip)
+        assert np.array_equal(h.tables(trip), ref)
+        assert np.array_equal(h.tables(trip, epi.PATH_POPC8), ref)
 
 
 def test_exact_ties_break_by_index():
@@ -98,16 +113,20 @@ def test_exact_ties_break_by_index():
     g[free[-1]] = g[k]
     g[free[0]] = g[i]
     with epi.Handle(g, d.phenotype) as h:
-        tr, sc = h.scan(8)
         otr, osc, _ = oracle.scan_topk(g, d.phenotype, 8)
-        assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
-        assert sc[0] == sc[1]
+        for path in PATHS:
+            h.set_option("path", path)
+            tr, sc = h.scan(8)
+            assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+            assert sc[0] == sc[1]
 
 
-def test_scan_range_slices_merge_to_full_scan():
+@pytest.mark.parametrize("path", PATHS)
+def test_scan_range_slices_merge_to_full_scan(path):
     g, ph = pins.tiny_data(80, 300, 150, seed=9)
     k = 12
     with epi.Handle(g, ph) as h:
+        h.set_option("path", path)
         full_t, full_s = h.scan(k)
         npairs = 80 * 79 // 2
         cuts = [0, 5, 400, 1000, 2500, npairs]
@@ -174,17 +193,20 @@ def test_injected_allocation_failure(monkeypatch):
         assert h.scan(3)[0].shape == (3, 3)
 
 
-def sampled_parity(d, n_sample, k, seed=0):
+def sampled_parity(d, n_sample, k, seed=0, path="popc8"):
     """Full-size workload: exact tables and scores on a random sample, the GPU's
     top-k rescored by the oracle, and no sampled triplet beating the k-th."""
     g, ph = d.genotypes, d.phenotype
     with epi.Handle(g, ph) as h:
+        h.set_option("path", path)
         tr, sc = h.scan(k)
         st = h.stats()
         samp = gen.random_triplets(d.n_snps, n_sample, seed=seed)
         planted = np.array(d.planted, dtype=np.int32).reshape(-1, 3)
         test_t = np.concatenate([samp, tr, planted])
-        assert np.array_equal(h.tables(test_t[:20000]), oracle.tables(g, ph, test_t[:20000]))
+        ref_tab = oracle.tables(g, ph, test_t[:20000])
+        assert np.array_equal(h.tables(test_t[:20000]), ref_tab)
+        assert np.array_equal(h.tables(test_t[:20000], epi.PATH_POPC8), ref_tab)
         s32, s64 = h.scores(test_t)
     ref = oracle.scores(g, ph, test_t)
     assert np.array_equal(s64, ref)
@@ -199,9 +221,10 @@ def sampled_parity(d, n_sample, k, seed=0):
     return st
 
 
-def test_medium_config_sampled():
+@pytest.mark.parametrize("path", PATHS)
+def test_medium_config_sampled(path):
     d = gen.make_config("medium")
-    st = sampled_parity(d, 200_000, 10)
+    st = sampled_parity(d, 200_000, 10, path=path)
     assert st["n_triplets"] == gen.n_triplets(1024)
 
 

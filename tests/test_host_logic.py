@@ -1,0 +1,20 @@
+"""Host-side checks of library code that needs no GPU: the exact 8 -> 27 cell
+derivation (compiled as host code with nvcc) against brute-force counting."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_derive27_matches_bruteforce(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "derive27_check"
+    subprocess.check_call([nvcc, "-std=c++17", "-o", str(exe),
+                           os.path.join(HERE, "host", "derive27_check.cu")])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and "derive27 ok" in out.stdout, out.stdout + out.stderr
