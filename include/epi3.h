@@ -138,6 +138,14 @@ int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k
                 double* out_k2_f64);
 
 /*
+ * Debug / test: the FP32 K2 that the scan kernel of `path` (EPI3_PATH_*) computes for
+ * every triplet i < j < k, written to out_scores[(i * M + j) * M + k] (other entries NaN),
+ * so the scan kernels' tables can be checked against epi3_scores for every triplet.
+ * out_scores holds M^3 floats; n_snps <= 512.  Pointer kind as epi3_tables.
+ */
+int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
+
+/*
  * Options (strings): "path" = "auto" | "popc" | "popc8" | "mma" | "mma16"; "threads" =
  * threads per block of
  * the scan kernel (64..512, multiple of 32); "ctas_per_sm" = persistent CTAs

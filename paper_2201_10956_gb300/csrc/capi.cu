@@ -93,6 +93,7 @@ struct epi3_handle {
     int oh_fp8 = -1;              // element type d_oh was built for (-1: none)
     int oh_ks[2] = {0, 0};
     long long oh_off1 = 0;
+    float* dbg = nullptr;         // device buffer of epi3_scan_scores (during that call only)
     int4* d_tiles = nullptr;      // tile list of the tensor-core form
     long long n_tiles = 0, tiles_pb = -1, tiles_pe = -1;
     Ctrl* h_ctrl = nullptr;       // pinned
@@ -357,6 +358,8 @@ int finish_scan(epi3_handle* h, int top_k, int attempt) {
         CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
         return 1;
     }
+    if (st & kStBadCount)
+        return fail(EPI3_ERR_CUDA, "tensor-core tables failed their range check (status %d)", st);
     if (st & kStFinalOverflow)
         return fail(EPI3_ERR_OVERFLOW,
                     "more than %d triplets lie within the FP32 error band of the k-th best",
@@ -393,7 +396,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
         CK(cudaEventRecord(h->ev[1], h->stream), "event");
         CK(launch_scan_mma(h->pl, h->k2, h->ptab, h->d_oh, h->oh_off1, h->oh_ks[0], h->oh_ks[1],
                            h->d_tiles, h->n_tiles, pb, pe, h->d_ctrl, h->d_cand, h->cand_cap, top_k,
-                           fp8, grid, h->stream), "mma scan launch");
+                           fp8, grid, h->dbg, h->stream), "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
         if (rc == 1) continue;
@@ -471,6 +474,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         a.pair_begin = pb;
         a.pair_end = pe;
         a.top_k = top_k;
+        a.dbg = h->dbg;
         CK(cudaEventRecord(h->ev[1], h->stream), "event");
         if (path == EPI3_PATH_POPC8) CK(launch_scan_popc8(a, grid, block, smem, h->stream), "scan launch");
         else CK(launch_scan_popc(a, grid, block, smem, h->stream), "scan launch");
@@ -675,6 +679,38 @@ int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k
     g_err.clear();
     if (n > 0 && !out_k2_f32 && !out_k2_f64) return fail(EPI3_ERR_ARG, "no output requested");
     return per_triplet(h, n, triplets, nullptr, out_k2_f32, out_k2_f64, EPI3_PATH_POPC);
+}
+
+int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores) {
+    g_err.clear();
+    if (!h || !out_scores) return fail(EPI3_ERR_ARG, "null argument");
+    if (h->M > 512) return fail(EPI3_ERR_ARG, "epi3_scan_scores needs n_snps <= 512");
+    const size_t n = (size_t)h->M * h->M * h->M;
+    const bool dev = (h->flags & EPI3_DEVICE_PTRS) != 0;
+    float* buf = nullptr;
+    if (dev) {
+        buf = out_scores;
+    } else {
+        CK(dev_alloc((void**)&buf, n * sizeof(float)), "alloc score cube");
+    }
+    cudaError_t e = cudaMemsetAsync(buf, 0xFF, n * sizeof(float), h->stream);  // NaN
+    const int saved = h->path;
+    int rc = e == cudaSuccess ? EPI3_OK : cuda_fail(e, "clear score cube");
+    if (rc == EPI3_OK) {
+        h->path = path;
+        h->dbg = buf;
+        int32_t trip[3];
+        double sc;
+        rc = scan_impl(h, 0, pairs(h->M), 1, trip, &sc, nullptr, true);
+        h->dbg = nullptr;
+        h->path = saved;
+    }
+    if (rc == EPI3_OK && !dev) {
+        e = cudaMemcpy(out_scores, buf, n * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "read score cube");
+    }
+    if (!dev) cudaFree(buf);
+    return rc;
 }
 
 int epi3_set_option(epi3_handle* h, const char* key, const char* value) {

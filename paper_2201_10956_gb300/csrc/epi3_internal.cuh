@@ -24,6 +24,7 @@ constexpr int kStFinalOverflow = 8;
 constexpr int kStInternal = 16;
 constexpr int kStBadIndex = 32;
 constexpr int kStTimeout = 64;
+constexpr int kStBadCount = 128;  // a tensor-core table failed its range check
 
 // Device control block of one scan.  Zeroed (then thr set to +inf) before each scan.
 struct Ctrl {
@@ -85,6 +86,7 @@ struct ScanArgs {
     long long cand_cap;
     long long pair_begin, pair_end;
     int top_k;
+    float* dbg;                   // optional: FP32 score of every triplet at (i*M + j)*M + k
 };
 
 // launchers (return cudaError_t of the launch)
@@ -117,7 +119,7 @@ cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTabl
                             const uint8_t* oh, long long off1, int KS0, int KS1, const int4* tiles,
                             long long n_tiles, long long pair_begin, long long pair_end, Ctrl* ctrl,
                             Cand* cand, long long cand_cap, int top_k, bool fp8, int grid,
-                            cudaStream_t st);
+                            float* dbg, cudaStream_t st);
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 
 // Message returned by epi3_last_error() on this thread.

@@ -175,6 +175,7 @@ int scan_noalloc(const uint8_t* geno, const uint8_t* pheno, int M, int N, int to
     a.pair_begin = 0;
     a.pair_end = (long long)(M - 1) * (M - 2) / 2;
     a.top_k = top_k;
+    a.dbg = nullptr;
     NA_CK(launch_reset(ctrl, st), "reset launch");
     NA_CK(launch_scan_popc(a, sms * occ, 128, smem, st), "scan launch");
     NA_CK(launch_select(ctrl, cand, kNoAllocCandCap, top_k, k2.rel, k2.abs_, st), "select launch");

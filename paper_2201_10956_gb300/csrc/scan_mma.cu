@@ -40,7 +40,7 @@ constexpr int kPrefetch = 4;             // producer prefetch distance (stages)
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
 constexpr int kCandCapMma = 1024;
 constexpr int kRoundMax = 2 * kEpiThreads;   // appends per epilogue round at most
-constexpr int kStTimeoutBit = 64;
+
 
 struct MmaArgs {
     Planes pl;
@@ -56,6 +56,7 @@ struct MmaArgs {
     Cand* cand;
     long long cand_cap;
     int top_k;
+    float* dbg;              // optional: FP32 score of every triplet at (i*M + j)*M + k
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -286,15 +287,16 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
     uint8_t* sA = base;
     uint8_t* sB = base + kStages * kChunk;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * kStages * kChunk);
-    // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], acc_empty[2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
+    // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], acc_empty[2], drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     EpiShared& es = *reinterpret_cast<EpiShared*>(base + 2 * kStages * kChunk + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t fullA0 = smem_u32(bars), fullB0 = smem_u32(bars + kStages),
                    empty0 = smem_u32(bars + 2 * kStages), accF0 = smem_u32(bars + 3 * kStages),
-                   accE0 = smem_u32(bars + 3 * kStages + 2);
+                   accE0 = smem_u32(bars + 3 * kStages + 2),
+                   drain0 = smem_u32(bars + 3 * kStages + 4);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -306,6 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
             mbar_init(accF0 + 8 * b, 1);
             mbar_init(accE0 + 8 * b, kEpiWarps);
         }
+        mbar_init(drain0, 1);
         *abort_flag = 0;
         es.cnt = 0;
         es.stop = 0;
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
     const long long n_steps = my_tiles * steps_per_tile;
     auto fail = [&]() {
         *abort_flag = 1;
-        atomicOr(&a.ctrl->status, kStTimeoutBit);
+        atomicOr(&a.ctrl->status, kStTimeout);
     };
 
     if (warp == 0) {
@@ -393,6 +396,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
                 }
                 if (ok) tc_commit(accF0 + 8 * buf);
             }
+            // every MMA issued must complete before TMEM is released
+            tc_commit(drain0);
+            volatile int no_abort = 0;
+            mbar_wait(drain0, 0, &no_abort);
         }
     } else if (warp >= kProdWarp0) {
         // ------------------------------------------------ B producers: row r = (jj, a, b)
@@ -513,7 +520,18 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
                                  __ldg(a.pt.marg + (size_t)c * M + j), mz[c], a.pt.n_c[c],
                                  c ? r1 : r0);
                     }
+                    // guard the log-factorial lookups: every cell must lie in [0, N_c]
+                    bool sane = true;
+#pragma unroll
+                    for (int q = 0; q < kCells; ++q)
+                        sane &= (unsigned)r0[q] <= (unsigned)a.pt.n_c[0] &&
+                                (unsigned)r1[q] <= (unsigned)a.pt.n_c[1];
+                    if (!sane) {
+                        atomicOr(&a.ctrl->status, kStBadCount);
+                        continue;
+                    }
                     const float s = k2_f32(r0, r1, a.k2.lf2);
+                    if (a.dbg) a.dbg[((size_t)i * M + j) * M + k] = s;
                     if (s <= fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr))) {
                         const int idx = atomicAdd(&es.cnt, 1);
                         es.buf[idx] = Cand{s, i, j, k};
@@ -574,7 +592,7 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
 }  // namespace
 
 size_t scan_mma_smem() {
-    return 1024 + 2 * kStages * kChunk + 256 + sizeof(EpiShared) + 64;
+    return 1024 + 2 * kStages * kChunk + 256 + sizeof(EpiShared) + 64;  // bars + slot < 256 B
 }
 
 int mma_samples_per_step(bool fp8) { return fp8 ? 128 : 64; }
@@ -593,7 +611,7 @@ cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTabl
                             const uint8_t* oh, long long off1, int KS0, int KS1, const int4* tiles,
                             long long n_tiles, long long pair_begin, long long pair_end, Ctrl* ctrl,
                             Cand* cand, long long cand_cap, int top_k, bool fp8, int grid,
-                            cudaStream_t st) {
+                            float* dbg, cudaStream_t st) {
     MmaArgs a;
     a.pl = pl;
     a.k2 = k2;
@@ -611,6 +629,7 @@ cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTabl
     a.cand = cand;
     a.cand_cap = cand_cap;
     a.top_k = top_k;
+    a.dbg = dbg;
     const size_t smem = scan_mma_smem();
     cudaError_t e;
     if (fp8) {

@@ -216,6 +216,7 @@ scan_popc_kernel(const ScanArgs a) {
                     count_class(a.pl, 1, k, sxy1, r1);
                 }
                 const float s = k2_f32(r0, r1, a.k2.lf2);
+                if (a.dbg) a.dbg[((size_t)i * M + j) * M + k] = s;
                 if (s <= fminf(s_tloc, s_tglob)) {
                     const int idx = atomicAdd(&s_cnt, 1);
                     cbuf[idx] = Cand{s, i, j, k};

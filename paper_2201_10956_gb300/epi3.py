@@ -27,7 +27,7 @@ MAX_TOPK = 512
 # Every symbol the header declares; tests check the library exports all of them.
 SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_destroy", "epi3_last_error",
            "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
-           "epi3_scan_noalloc")
+           "epi3_scan_noalloc", "epi3_scan_scores")
 
 
 class Epi3Error(RuntimeError):
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
         "epi3_get_shape": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
                            ctypes.POINTER(I32)],
         "epi3_scan_noalloc": [P, P, I32, I32, I32, P, P, P],
+        "epi3_scan_scores": [P, I32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -197,6 +198,14 @@ class Handle:
         s64 = self._alloc((t.shape[0],), np.float64)
         _check(load().epi3_scores(self._h, int(t.shape[0]), _ptr(t), _ptr(s32), _ptr(s64)))
         return s32, s64
+
+    def scan_scores(self, path: int):
+        """FP32 K2 the scan kernel of `path` computes for every triplet: [M, M, M], NaN off
+        the i < j < k entries (M <= 512)."""
+        m = self.n_snps
+        out = self._alloc((m, m, m), np.float32)
+        _check(load().epi3_scan_scores(self._h, int(path), _ptr(out)))
+        return out
 
     def set_option(self, key: str, value):
         _check(load().epi3_set_option(self._h, key.encode(), str(value).encode()))

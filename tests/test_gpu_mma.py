@@ -1,0 +1,116 @@
+"""Tensor-core (tcgen05) scan and the 8-cell POPC scan vs the oracle (needs an sm_103 GPU).
+
+The scan kernels' own FP32 scores for every triplet (epi3_scan_scores) must equal the FP32
+score of the exact table (epi3_scores) bit for bit -- so every table the kernel counted is
+exact -- and the FP64-rescored top-k must equal the oracle's.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import oracle_pins as pins
+from paper_2201_10956_gb300 import build as B
+import paper_2201_10956_gb300 as epi
+
+pytestmark = pytest.mark.gpu
+
+KERNEL_PATHS = [("popc", epi.PATH_POPC), ("popc8", epi.PATH_POPC8), ("mma", epi.PATH_MMA),
+                ("mma16", epi.PATH_MMA16)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    return epi.load()
+
+
+def all_trip(m):
+    return np.array(list(itertools.combinations(range(m), 3)), dtype=np.int32).reshape(-1, 3)
+
+
+def check_every_triplet(h, g, ph, path_id):
+    m = g.shape[0]
+    cube = h.scan_scores(path_id)
+    trip = all_trip(m)
+    got = cube[trip[:, 0], trip[:, 1], trip[:, 2]]
+    s32, _ = h.scores(trip)
+    bad = np.nonzero(~(got == s32))[0]
+    assert bad.size == 0, (path_id, bad.size, trip[bad[:5]], got[bad[:5]], s32[bad[:5]])
+
+
+@pytest.mark.parametrize("name,path_id", KERNEL_PATHS)
+@pytest.mark.parametrize("m,n,n1", [(3, 5, 2), (7, 130, 64), (40, 512, 256), (70, 1000, 401),
+                                    (97, 257, 0), (65, 300, 300), (130, 200, 77)])
+def test_scan_kernel_tables_exact(name, path_id, m, n, n1):
+    g, ph = pins.tiny_data(m, n, n1, seed=1000 + m + n)
+    with epi.Handle(g, ph) as h:
+        check_every_triplet(h, g, ph, path_id)
+        h.set_option("path", name)
+        k = min(10, m * (m - 1) * (m - 2) // 6)
+        tr, sc = h.scan(k)
+        otr, osc, _ = oracle.scan_topk(g, ph, k)
+        assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("name,path_id", KERNEL_PATHS[2:])
+def test_tensor_counts_exact_at_large_counts(name, path_id):
+    # nearly monomorphic SNPs: one cell holds almost every sample of a class, so the
+    # accumulators reach ~N_c (here 16000 and 24000)
+    rng = np.random.default_rng(5)
+    m, n, n1 = 12, 40000, 24000
+    g = np.zeros((m, n), dtype=np.uint8)
+    g[rng.random((m, n)) < 0.002] = 1
+    ph = np.zeros(n, dtype=np.uint8)
+    ph[rng.choice(n, n1, replace=False)] = 1
+    with epi.Handle(g, ph) as h:
+        check_every_triplet(h, g, ph, path_id)
+        h.set_option("path", name)
+        tr, sc = h.scan(5)
+    otr, osc, _ = oracle.scan_topk(g, ph, 5)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("name", ["mma", "mma16"])
+def test_tensor_scan_tiny_config(name):
+    d = gen.make_config("tiny")
+    with epi.Handle(d.genotypes, d.phenotype) as h:
+        h.set_option("path", name)
+        tr, sc = h.scan(10)
+        assert h.stats()["path"] == (epi.PATH_MMA if name == "mma" else epi.PATH_MMA16)
+    otr, osc, _ = oracle.scan_topk(d.genotypes, d.phenotype, 10)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("name", ["mma", "mma16"])
+def test_tensor_scan_range_slices(name):
+    g, ph = pins.tiny_data(90, 400, 170, seed=19)
+    k = 9
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", name)
+        full_t, full_s = h.scan(k)
+        npairs = 90 * 89 // 2
+        rows = []
+        for a, b in zip([0, 7, 900, 2500], [7, 900, 2500, npairs]):
+            t, s = h.scan_range(a, b, k)
+            rows += [(float(x), *map(int, y)) for x, y in zip(s, t)]
+        rows.sort()
+        assert [r[1:] for r in rows[:k]] == [tuple(map(int, t)) for t in full_t]
+
+
+@pytest.mark.parametrize("name", ["mma", "mma16"])
+def test_tensor_scan_medium_sampled(name):
+    d = gen.make_config("medium")
+    g, ph = d.genotypes, d.phenotype
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", "popc8")
+        ref_t, ref_s = h.scan(10)
+        h.set_option("path", name)
+        tr, sc = h.scan(10)
+    assert np.array_equal(tr, ref_t) and np.array_equal(sc, ref_s)
+    assert np.array_equal(oracle.scores(g, ph, tr), sc)
