@@ -136,6 +136,43 @@ def shard_pairs(m, world, rank):
     return pair_at(lo_t), pair_at(hi_t)
 
 
+PATH_NAMES = {1: "popc", 2: "popc8", 3: "mma", 4: "mma16"}
+DTYPES = {1: "u32 popc / int32 counts", 2: "u32 popc / int32 counts",
+          3: "e4m3 0/1 x e4m3 0/1 -> fp32 (exact integer counts)",
+          4: "f16 0/1 x f16 0/1 -> fp32 (exact integer counts)"}
+
+
+def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config):
+    """Roofline of the dominant kernel, from algorithmic work per launch.
+
+    POPC forms: 27 (paper's form) or 8 (8-cell form) 32-bit POPC per 32-sample word and
+    class, i.e. cells/32 POPC per sample-triplet; peak = SMs x max SM clock x 16 POPC/SM/clk.
+    Tensor forms: 8 useful MACs = 16 FLOP per sample-triplet; peak = the measured dense bf16
+    rate (fp16 runs at the bf16 rate; e4m3 at 2x, the nominal fp8/bf16 ratio).
+    """
+    units = gen.n_triplets(m) * n / world          # sample-triplets per launch
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    traffic = TRAFFIC.get((PATH_NAMES.get(path), config))
+    if path in (3, 4):
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 * (2.0 if path == 3 else 1.0)
+        achieved = units * 16.0 / kern_s / 1e12
+        return {"bound": "tensor", "kernel": f"scan_mma_kernel<{'e4m3' if path == 3 else 'f16'}>",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst)"
+                             + (" x 2 (e4m3/bf16 nominal ratio)" if path == 3 else ""),
+                "work_note": "16 FLOP (8 useful 0/1 MACs) per sample-triplet; tile waste excluded"}
+    cells = 8.0 if path == 2 else 27.0
+    achieved = units * cells / 32.0 / kern_s
+    peak = n_sm * sm_max * 1e6 * POPC_PER_SM_CLK
+    return {"bound": "alu", "kernel": f"scan_popc_kernel<{'8-cell' if path == 2 else '27-cell'}>",
+            "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TPOPC/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_note": f"{n_sm} SMs x {sm_max:.0f} MHz x {POPC_PER_SM_CLK} POPC/SM/clk",
+            "work_note": f"{cells:.0f}/32 POPC per sample-triplet"}
+
+
 def merge_topk(rows, k):
     rows = sorted(rows)
     return rows[:k]
@@ -286,25 +323,15 @@ def run_ours(args, rank, world, local_rank):
 
     props = torch.cuda.get_device_properties(local_rank)
     peaks = read_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     kern_s = statistics.mean(kern_ms) / 1000.0
-    cells = 8.0 if st["path"] == 2 else 27.0            # POPC per 32-sample word and class
-    popc_alg = gen.n_triplets(m) * n * cells / 32.0     # 32-bit POPC per launch
-    if world > 1:
-        popc_alg /= world
-    peak_popc = props.multi_processor_count * sm_max * 1e6 * POPC_PER_SM_CLK
-    achieved = popc_alg / kern_s
-    traffic = TRAFFIC.get((args.path, args.config))
-    kname = "scan_popc_kernel<true> (8-cell)" if st["path"] == 2 else "scan_popc_kernel<false> (27-cell)"
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
-                "peak": peak_popc / 1e12, "unit": "TPOPC/s", "frac": achieved / peak_popc,
-                "traffic": traffic,
-                "peak_note": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
-                             f"{POPC_PER_SM_CLK} POPC/SM/clk",
-                "kernel_ms": 1000 * kern_s, "select_ms": statistics.mean(sel_ms)}
+    roofline = roofline_of(st["path"], m, n, world, kern_s, props.multi_processor_count, peaks,
+                           args.config)
+    roofline["kernel_ms"] = 1000 * kern_s
+    roofline["select_ms"] = statistics.mean(sel_ms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps,
-            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": DTYPES[st["path"]],
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "path": args.path,
                        "top_k": k, "l2": "flushed before every timed step (512 MB write)",

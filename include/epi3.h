@@ -49,9 +49,10 @@ extern "C" {
 #define EPI3_PATH_AUTO 0
 #define EPI3_PATH_POPC 1  /* 27-cell LOP3 AND + POPC over bit planes (Alg. 2 counting) */
 #define EPI3_PATH_POPC8 2 /* 8 cells (genotypes 0/1) by AND + POPC, 19 derived exactly from
-                             pair tables and marginals; the default (auto) scan path */
+                             pair tables and marginals */
 #define EPI3_PATH_MMA 3   /* tensor cores: the 8 cells as a GEMM of one-hot 0/1 E4M3 operands
-                             (tcgen05 kind::f8f6f4, FP32 accumulation), 19 derived */
+                             (tcgen05 kind::f8f6f4, FP32 accumulation), 19 derived; the default
+                             (auto) scan path up to about 8700 SNPs, POPC8 beyond */
 #define EPI3_PATH_MMA16 4 /* the same GEMM with FP16 operands (tcgen05 kind::f16) */
 
 #define EPI3_MAX_TOPK 512

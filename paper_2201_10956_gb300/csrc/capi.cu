@@ -323,8 +323,15 @@ int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
     return EPI3_OK;
 }
 
+// Tiles of the tensor-core form for M SNPs (about M^3 / 12288); the host tile list caps it.
+long long mma_tile_estimate(long long M) { return M * M * M / 12288 + 1; }
+constexpr long long kMaxMmaTiles = 1LL << 26;
+
+// auto: the tensor-core form (E4M3 operands) when its tile list is small enough, else the
+// 8-cell POPC form.
 int resolve_path(const epi3_handle* h) {
-    return h->path == EPI3_PATH_AUTO ? EPI3_PATH_POPC8 : h->path;
+    if (h->path != EPI3_PATH_AUTO) return h->path;
+    return mma_tile_estimate(h->M) <= kMaxMmaTiles ? EPI3_PATH_MMA : EPI3_PATH_POPC8;
 }
 
 // Candidate stage + result read-back shared by both scan forms.  Returns 1 to retry with a
@@ -443,6 +450,8 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         path != EPI3_PATH_MMA16)
         return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
     const bool mma = path == EPI3_PATH_MMA || path == EPI3_PATH_MMA16;
+    if (mma && mma_tile_estimate(h->M) > kMaxMmaTiles)
+        return fail(EPI3_ERR_UNSUPPORTED, "n_snps %d too large for the tensor-core tile list", h->M);
     if (path != EPI3_PATH_POPC) {
         int rc = ensure_pair_tables(h);
         if (rc == EPI3_OK && mma) rc = ensure_onehot(h, path == EPI3_PATH_MMA);
