@@ -203,6 +203,41 @@ int epi3_scan_noalloc(const uint8_t* genotypes, const uint8_t* phenotype, int32_
                       int32_t n_samples, int32_t top_k, int32_t* out_triplets,
                       double* out_scores, void* cuda_stream);
 
+/*
+ * Batches: many independent data sets ("cohorts") of uneven size scanned together.  Each
+ * cohort is packed like epi3_create; a tuner times the tensor-core and 8-cell POPC scan
+ * kernels on each cohort's heaviest pair slice and keeps the faster (per M/64, N/1024
+ * bucket; persisted in the file named by EPI3_TUNE_CACHE; EPI3_BATCH_PATH=mma|popc8
+ * forces one).  The tensor-core cohorts share ONE persistent tcgen05 launch over all their
+ * tiles; the whole scan + candidate stages + read-back is captured once in a CUDA graph and
+ * replayed by every epi3_batch_scan.  The answer of each cohort is the one epi3_scan gives.
+ *
+ *   cohorts[c]    {genotypes, phenotype, n_snps, n_samples} as epi3_create.
+ *   flags         0 or EPI3_DEVICE_PTRS (inputs and outputs are device memory).
+ *   out_triplets  [n_cohorts][top_k][3];  out_scores [n_cohorts][top_k].
+ *   top_k         1..min(EPI3_MAX_TOPK, C(M,3) of every cohort).
+ */
+typedef struct {
+    const uint8_t* genotypes;
+    const uint8_t* phenotype;
+    int32_t n_snps;
+    int32_t n_samples;
+} epi3_cohort;
+
+typedef struct epi3_batch epi3_batch;
+
+int epi3_batch_create(epi3_batch** b, int32_t n_cohorts, const epi3_cohort* cohorts,
+                      int32_t flags, void* cuda_stream);
+int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double* out_scores);
+int epi3_batch_destroy(epi3_batch* b);
+/* Figures of the last epi3_batch_scan (pack_ms holds the tuner's time at create). */
+int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out);
+/* The path (EPI3_PATH_MMA or EPI3_PATH_POPC8) the tuner chose for each cohort. */
+int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths);
+/* One-shot: epi3_batch_create + epi3_batch_scan + epi3_batch_destroy. */
+int epi3_scan_batch(int32_t n_cohorts, const epi3_cohort* cohorts, int32_t top_k,
+                    int32_t* out_triplets, double* out_scores, int32_t flags, void* cuda_stream);
+
 /* Shape of a handle: M, N, controls, cases. */
 int epi3_get_shape(const epi3_handle* h, int32_t* n_snps, int32_t* n_samples,
                    int32_t* n_controls, int32_t* n_cases);

@@ -94,6 +94,7 @@ struct epi3_handle {
     int oh_ks[2] = {0, 0};
     long long oh_off1 = 0;
     float* dbg = nullptr;         // device buffer of epi3_scan_scores (during that call only)
+    CohortDev* d_cd = nullptr;    // this data set's descriptor for the tensor-core kernel
     int4* d_tiles = nullptr;      // tile list of the tensor-core form
     long long n_tiles = 0, tiles_pb = -1, tiles_pe = -1;
     Ctrl* h_ctrl = nullptr;       // pinned
@@ -124,6 +125,7 @@ void release(epi3_handle* h) {
     cudaFree(h->d_marg);
     cudaFree(h->d_oh);
     cudaFree(h->d_tiles);
+    cudaFree(h->d_cd);
     cudaFreeHost(h->h_ctrl);
     cudaFreeHost(h->h_scores);
     cudaFreeHost(h->h_trip);
@@ -292,12 +294,8 @@ int ensure_onehot(epi3_handle* h, bool fp8) {
 
 // Tiles (i, 32-SNP block of j, 64-SNP block of k) holding a triplet i<j<k whose pair (i, j)
 // lies in [pb, pe); third-SNP block outermost so concurrent CTAs share A chunks in L2.
-int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
-    if (h->d_tiles && h->tiles_pb == pb && h->tiles_pe == pe) return EPI3_OK;
-    cudaFree(h->d_tiles);
-    h->d_tiles = nullptr;
-    const int M = h->M, kbc = (M + 63) / 64, jbc = (M + 31) / 32;
-    std::vector<int4> t;
+void append_tiles(int M, long long pb, long long pe, int cohort, std::vector<int4>& t) {
+    const int kbc = (M + 63) / 64, jbc = (M + 31) / 32;
     for (int kb = 0; kb < kbc; ++kb) {
         const int k_hi = std::min(64 * kb + 63, M - 1);
         for (int jb = 0; jb < jbc; ++jb) {
@@ -308,10 +306,18 @@ int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
                 const long long jmin = std::max(j_lo, i + 1), jmax = std::min(j_hi, k_hi - 1);
                 const long long pmin = jmin * (jmin - 1) / 2 + i, pmax = jmax * (jmax - 1) / 2 + i;
                 if (pmin >= pe || pmax < pb) continue;
-                t.push_back(make_int4(i, jb, kb, 0));
+                t.push_back(make_int4(i, jb, kb, cohort));
             }
         }
     }
+}
+
+int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
+    if (h->d_tiles && h->tiles_pb == pb && h->tiles_pe == pe) return EPI3_OK;
+    cudaFree(h->d_tiles);
+    h->d_tiles = nullptr;
+    std::vector<int4> t;
+    append_tiles(h->M, pb, pe, 0, t);
     h->n_tiles = (long long)t.size();
     CK(dev_alloc((void**)&h->d_tiles, sizeof(int4) * (t.empty() ? 1 : t.size())), "alloc tiles");
     if (!t.empty())
@@ -392,18 +398,39 @@ int copy_out(epi3_handle* h, int32_t* out_trip, double* out_scores, int32_t* n_o
     return EPI3_OK;
 }
 
+CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k) {
+    CohortDev cd{};
+    cd.pl = h->pl;
+    cd.k2 = h->k2;
+    cd.pt = h->ptab;
+    cd.oh = h->d_oh;
+    cd.oh_off1 = h->oh_off1;
+    cd.KS[0] = h->oh_ks[0];
+    cd.KS[1] = h->oh_ks[1];
+    cd.pair_begin = pb;
+    cd.pair_end = pe;
+    cd.ctrl = h->d_ctrl;
+    cd.cand = h->d_cand;
+    cd.cand_cap = h->cand_cap;
+    cd.top_k = top_k;
+    cd.dbg = h->dbg;
+    return cd;
+}
+
 int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long long nt, int top_k,
                   int32_t* out_trip, double* out_scores, int32_t* n_out) {
     const bool fp8 = path == EPI3_PATH_MMA;
+    if (!h->d_cd) CK(dev_alloc((void**)&h->d_cd, sizeof(CohortDev)), "alloc descriptor");
     const int grid = h->sm_count;
     for (int attempt = 0;; ++attempt) {
         if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
         CK(cudaEventRecord(h->ev[0], h->stream), "event");
         CK(launch_reset(h->d_ctrl, h->stream), "reset launch");
         CK(cudaEventRecord(h->ev[1], h->stream), "event");
-        CK(launch_scan_mma(h->pl, h->k2, h->ptab, h->d_oh, h->oh_off1, h->oh_ks[0], h->oh_ks[1],
-                           h->d_tiles, h->n_tiles, pb, pe, h->d_ctrl, h->d_cand, h->cand_cap, top_k,
-                           fp8, grid, h->dbg, h->stream), "mma scan launch");
+        const CohortDev cd = cohort_of(h, pb, pe, top_k);
+        CK(cudaMemcpyAsync(h->d_cd, &cd, sizeof(cd), cudaMemcpyHostToDevice, h->stream),
+           "upload descriptor");
+        CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, fp8, grid, h->stream), "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
         if (rc == 1) continue;
@@ -767,6 +794,423 @@ int epi3_get_shape(const epi3_handle* h, int32_t* n_snps, int32_t* n_samples,
     if (n_controls) *n_controls = h->N0;
     if (n_cases) *n_cases = h->N1;
     return EPI3_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batches
+//
+// Many independent data sets ("cohorts") of uneven shape scanned together: every cohort is
+// packed into its own handle; the cohorts the tuner gives to the tensor-core form share ONE
+// persistent tcgen05 launch over the concatenated tile list (tile.w = cohort), the others
+// run the 8-cell POPC scan; each cohort then has its own candidate stage.  The whole
+// sequence is captured once into a CUDA graph and replayed by every epi3_batch_scan.
+
+struct epi3_batch {
+    int n = 0;
+    int device = 0, sm_count = 0, flags = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<epi3_handle*> h;
+    std::vector<int> path;              // EPI3_PATH_MMA or EPI3_PATH_POPC8 per cohort
+    Ctrl* d_ctrls = nullptr;            // one control block per cohort, contiguous
+    Ctrl* h_ctrls = nullptr;            // pinned
+    CohortDev* d_cds = nullptr;
+    int4* d_tiles = nullptr;
+    long long n_tiles = 0;
+    double* d_scores = nullptr;         // [n][EPI3_MAX_TOPK]
+    int* d_trip = nullptr;
+    double* h_scores = nullptr;         // pinned
+    int* h_trip = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_k = -1;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    epi3_stats stats{};
+    float tune_ms = 0.f;
+};
+
+namespace {
+
+void batch_release(epi3_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (epi3_handle* h : b->h) {
+        if (!h) continue;
+        h->d_ctrl = nullptr;  // owned by the batch
+        release(h);
+    }
+    cudaFree(b->d_ctrls);
+    cudaFreeHost(b->h_ctrls);
+    cudaFree(b->d_cds);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_scores);
+    cudaFree(b->d_trip);
+    cudaFreeHost(b->h_scores);
+    cudaFreeHost(b->h_trip);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// ---------------------------------------------------------------- path tuner
+// The faster of the tensor-core and 8-cell POPC forms for a cohort shape, measured: both
+// scan kernels are timed on the cohort's heaviest pair slice (pairs with the smallest j,
+// about 1/16 of the pairs) and the lower kernel time per triplet wins.  Results are kept
+// per (M / 64, N / 1024) bucket for the process, and in the file named by EPI3_TUNE_CACHE
+// (lines "device<TAB>SMs<TAB>M/64<TAB>N/1024<TAB>path") across processes.
+struct TuneEntry {
+    std::string dev;
+    int sms, mb, nb, path;
+};
+std::vector<TuneEntry> g_tune;
+bool g_tune_loaded = false;
+
+std::string device_name(int dev) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    return p.name;
+}
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* f = getenv("EPI3_TUNE_CACHE");
+    if (!f) return;
+    FILE* fp = fopen(f, "r");
+    if (!fp) return;
+    char line[512];
+    while (fgets(line, sizeof(line), fp)) {
+        char name[256];
+        TuneEntry e;
+        if (sscanf(line, "%255[^\t]\t%d\t%d\t%d\t%d", name, &e.sms, &e.mb, &e.nb, &e.path) == 5) {
+            e.dev = name;
+            g_tune.push_back(e);
+        }
+    }
+    fclose(fp);
+}
+
+void tune_store(const TuneEntry& e) {
+    g_tune.push_back(e);
+    const char* f = getenv("EPI3_TUNE_CACHE");
+    if (!f) return;
+    FILE* fp = fopen(f, "a");
+    if (!fp) return;
+    fprintf(fp, "%s\t%d\t%d\t%d\t%d\n", e.dev.c_str(), e.sms, e.mb, e.nb, e.path);
+    fclose(fp);
+}
+
+int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
+    const char* force = getenv("EPI3_BATCH_PATH");
+    if (force && !strcmp(force, "mma")) { *path_out = EPI3_PATH_MMA; return EPI3_OK; }
+    if (force && !strcmp(force, "popc8")) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
+    if (mma_tile_estimate(h->M) > kMaxMmaTiles) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
+    tune_load();
+    const std::string dev = device_name(b->device);
+    const int mb = h->M / 64, nb = h->N / 1024;
+    for (const TuneEntry& e : g_tune)
+        if (e.dev == dev && e.sms == b->sm_count && e.mb == mb && e.nb == nb) {
+            *path_out = e.path;
+            return EPI3_OK;
+        }
+    const long long np = pairs(h->M - 1);
+    const long long pe = std::max(1LL, np / 16);
+    float t[2] = {0.f, 0.f};
+    const int paths[2] = {EPI3_PATH_POPC8, EPI3_PATH_MMA};
+    int32_t trip[3];
+    double sc;
+    int32_t nout = 0;
+    for (int q = 0; q < 2; ++q) {
+        h->path = paths[q];
+        int rc = scan_impl(h, 0, pe, 1, trip, &sc, &nout, false);  // set-up + warm-up
+        if (rc == EPI3_OK) rc = scan_impl(h, 0, pe, 1, trip, &sc, &nout, false);
+        if (rc != EPI3_OK) return rc;
+        t[q] = h->stats.scan_kernel_ms;
+        *ms += h->stats.total_ms * 2;
+    }
+    h->path = EPI3_PATH_AUTO;
+    *path_out = t[1] <= t[0] ? EPI3_PATH_MMA : EPI3_PATH_POPC8;
+    tune_store(TuneEntry{dev, b->sm_count, mb, nb, *path_out});
+    return EPI3_OK;
+}
+
+int batch_capture(epi3_batch* b, int top_k) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    // descriptors of the tensor-core cohorts (candidate lists may have grown)
+    std::vector<CohortDev> cds(b->n);
+    for (int c = 0; c < b->n; ++c) {
+        epi3_handle* h = b->h[c];
+        cds[c] = cohort_of(h, 0, pairs(h->M - 1), top_k);
+    }
+    CK(cudaMemcpyAsync(b->d_cds, cds.data(), sizeof(CohortDev) * b->n, cudaMemcpyHostToDevice,
+                       b->stream), "upload descriptors");
+    // launch shapes and function attributes are settled before capture
+    std::vector<int> grid(b->n, 0);
+    std::vector<size_t> smem(b->n, 0);
+    for (int c = 0; c < b->n; ++c) {
+        if (b->path[c] != EPI3_PATH_POPC8) continue;
+        epi3_handle* h = b->h[c];
+        int occ = 0;
+        smem[c] = scan_popc8_smem(h->pl);
+        CK(scan_popc8_occupancy(h->threads, smem[c], &occ), "occupancy");
+        if (occ < 1) return fail(EPI3_ERR_UNSUPPORTED, "cohort %d does not fit the POPC scan", c);
+        grid[c] = b->sm_count * occ;
+    }
+    CK(cudaStreamSynchronize(b->stream), "descriptors");
+
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    cudaError_t err = cudaSuccess;
+    auto ok = [&](cudaError_t e) {
+        if (err == cudaSuccess && e != cudaSuccess) err = e;
+    };
+    for (int c = 0; c < b->n; ++c) ok(launch_reset(b->h[c]->d_ctrl, b->stream));
+    ok(cudaEventRecord(b->ev[1], b->stream));
+    if (b->n_tiles > 0) ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, true, b->sm_count, b->stream));
+    for (int c = 0; c < b->n; ++c) {
+        if (b->path[c] != EPI3_PATH_POPC8) continue;
+        epi3_handle* h = b->h[c];
+        ScanArgs a{};
+        a.pl = h->pl;
+        a.k2 = h->k2;
+        a.pt = h->ptab;
+        a.ctrl = h->d_ctrl;
+        a.cand = h->d_cand;
+        a.cand_cap = h->cand_cap;
+        a.pair_begin = 0;
+        a.pair_end = pairs(h->M - 1);
+        a.top_k = top_k;
+        a.dbg = nullptr;
+        ok(launch_scan_popc8(a, grid[c], h->threads, smem[c], b->stream));
+    }
+    ok(cudaEventRecord(b->ev[2], b->stream));
+    for (int c = 0; c < b->n; ++c) {
+        epi3_handle* h = b->h[c];
+        ok(launch_select(h->d_ctrl, h->d_cand, h->cand_cap, top_k, h->k2.rel, h->k2.abs_, b->stream));
+        ok(launch_rescore(h->pl, h->k2, h->d_ctrl, h->d_cand, h->cand_cap, h->d_fin,
+                          b->sm_count * 8, b->stream));
+        ok(launch_final(h->d_ctrl, h->d_fin, top_k, b->d_scores + (size_t)c * EPI3_MAX_TOPK,
+                        b->d_trip + (size_t)c * 3 * EPI3_MAX_TOPK, b->stream));
+    }
+    ok(cudaEventRecord(b->ev[3], b->stream));
+    ok(cudaMemcpyAsync(b->h_ctrls, b->d_ctrls, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToHost, b->stream));
+    ok(cudaMemcpyAsync(b->h_scores, b->d_scores, sizeof(double) * b->n * EPI3_MAX_TOPK,
+                       cudaMemcpyDeviceToHost, b->stream));
+    ok(cudaMemcpyAsync(b->h_trip, b->d_trip, sizeof(int) * 3 * b->n * EPI3_MAX_TOPK,
+                       cudaMemcpyDeviceToHost, b->stream));
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(err, "batch capture");
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "end capture");
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return cuda_fail(ei, "graph instantiate");
+    b->graph_k = top_k;
+    return EPI3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* cohorts,
+                      int32_t flags, void* cuda_stream) {
+    g_err.clear();
+    if (!out) return fail(EPI3_ERR_ARG, "null batch pointer");
+    *out = nullptr;
+    if (n_cohorts < 1 || !cohorts) return fail(EPI3_ERR_ARG, "need at least one cohort");
+    if (flags & ~EPI3_DEVICE_PTRS) return fail(EPI3_ERR_ARG, "unknown flags 0x%x", flags);
+    int dev = 0, sms = 0;
+    int rc = check_device(&dev, &sms);
+    if (rc != EPI3_OK) return rc;
+    epi3_batch* b = new epi3_batch();
+    b->n = n_cohorts;
+    b->device = dev;
+    b->sm_count = sms;
+    b->flags = flags;
+    cudaError_t e;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        batch_release(b);
+        return cuda_fail(e, "stream create");
+    } else {
+        b->own_stream = true;
+    }
+    auto bail = [&](int code) {
+        std::string msg = g_err;
+        batch_release(b);
+        g_err = msg;
+        return code;
+    };
+    for (auto& ev : b->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(e, "event create"));
+    if ((e = dev_alloc((void**)&b->d_ctrls, sizeof(Ctrl) * n_cohorts)) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc control blocks"));
+    if ((e = cudaMallocHost((void**)&b->h_ctrls, sizeof(Ctrl) * n_cohorts)) != cudaSuccess)
+        return bail(cuda_fail(e, "pinned control blocks"));
+    b->h.assign(n_cohorts, nullptr);
+    b->path.assign(n_cohorts, EPI3_PATH_POPC8);
+    for (int c = 0; c < n_cohorts; ++c) {
+        const epi3_cohort& co = cohorts[c];
+        rc = epi3_create(&b->h[c], co.genotypes, co.phenotype, co.n_snps, co.n_samples, flags,
+                         b->stream);
+        if (rc != EPI3_OK) {
+            g_err = "cohort " + std::to_string(c) + ": " + g_err;
+            return bail(rc);
+        }
+        epi3_handle* h = b->h[c];
+        cudaFree(h->d_ctrl);              // the batch keeps every control block together
+        h->d_ctrl = b->d_ctrls + c;
+        if ((rc = ensure_pair_tables(h)) != EPI3_OK) return bail(rc);
+    }
+    std::vector<int4> tiles;
+    for (int c = 0; c < n_cohorts; ++c) {
+        epi3_handle* h = b->h[c];
+        if ((rc = tune_path(b, h, &b->path[c], &b->tune_ms)) != EPI3_OK) return bail(rc);
+        if (b->path[c] == EPI3_PATH_MMA) {
+            if ((rc = ensure_onehot(h, true)) != EPI3_OK) return bail(rc);
+            append_tiles(h->M, 0, pairs(h->M - 1), c, tiles);
+        }
+        h->path = b->path[c];
+    }
+    b->n_tiles = (long long)tiles.size();
+    if ((e = dev_alloc((void**)&b->d_tiles, sizeof(int4) * (tiles.empty() ? 1 : tiles.size()))) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc tiles"));
+    if (!tiles.empty() &&
+        (e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload tiles"));
+    if ((e = dev_alloc((void**)&b->d_cds, sizeof(CohortDev) * n_cohorts)) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc descriptors"));
+    const size_t nk = (size_t)n_cohorts * EPI3_MAX_TOPK;
+    if ((e = dev_alloc((void**)&b->d_scores, sizeof(double) * nk)) != cudaSuccess ||
+        (e = dev_alloc((void**)&b->d_trip, sizeof(int) * 3 * nk)) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&b->h_scores, sizeof(double) * nk)) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&b->h_trip, sizeof(int) * 3 * nk)) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc batch outputs"));
+    *out = b;
+    return EPI3_OK;
+}
+
+int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double* out_scores) {
+    g_err.clear();
+    if (!b || !out_triplets || !out_scores) return fail(EPI3_ERR_ARG, "null argument");
+    if (top_k < 1 || top_k > EPI3_MAX_TOPK)
+        return fail(EPI3_ERR_ARG, "top_k %d outside 1..%d", top_k, EPI3_MAX_TOPK);
+    for (int c = 0; c < b->n; ++c) {
+        const long long m = b->h[c]->M;
+        if (top_k > m * (m - 1) * (m - 2) / 6)
+            return fail(EPI3_ERR_ARG, "top_k %d exceeds the triplets of cohort %d", top_k, c);
+    }
+    for (int attempt = 0;; ++attempt) {
+        if (!b->exec || b->graph_k != top_k) {
+            const int rc = batch_capture(b, top_k);
+            if (rc != EPI3_OK) return rc;
+        }
+        if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
+        CK(cudaEventRecord(b->ev[0], b->stream), "event");
+        CK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+        CK(cudaStreamSynchronize(b->stream), "batch scan");
+        bool grow = false;
+        for (int c = 0; c < b->n; ++c) {
+            const int st = b->h_ctrls[c].status;
+            epi3_handle* h = b->h[c];
+            if (st & kStTimeout) return fail(EPI3_ERR_TIMEOUT, "cohort %d: a bounded wait ran out", c);
+            if (st & kStBadCount) return fail(EPI3_ERR_CUDA, "cohort %d: table range check failed", c);
+            if (st & kStCandOverflow) {
+                if (h->cand_cap >= (1LL << 24) || attempt >= 3)
+                    return fail(EPI3_ERR_OVERFLOW, "cohort %d: more than %lld FP32 candidates", c,
+                                h->cand_cap);
+                cudaFree(h->d_cand);
+                h->d_cand = nullptr;
+                h->cand_cap *= 8;
+                CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
+                grow = true;
+            }
+            if (st & kStFinalOverflow)
+                return fail(EPI3_ERR_OVERFLOW, "cohort %d: more than %d near-tied candidates", c,
+                            kFinalCap);
+            if (st & (kStInternal | kStBadIndex))
+                return fail(EPI3_ERR_CUDA, "cohort %d: internal error (status %d)", c, st);
+        }
+        if (grow) {
+            b->graph_k = -1;  // candidate pointers changed: capture again
+            continue;
+        }
+        break;
+    }
+    const bool dev = (b->flags & EPI3_DEVICE_PTRS) != 0;
+    for (int c = 0; c < b->n; ++c) {
+        const int nout = (int)b->h_ctrls[c].n_out;
+        if (dev) {
+            CK(cudaMemcpyAsync(out_scores + (size_t)c * top_k, b->d_scores + (size_t)c * EPI3_MAX_TOPK,
+                               sizeof(double) * nout, cudaMemcpyDeviceToDevice, b->stream), "copy scores");
+            CK(cudaMemcpyAsync(out_triplets + (size_t)c * 3 * top_k, b->d_trip + (size_t)c * 3 * EPI3_MAX_TOPK,
+                               sizeof(int) * 3 * nout, cudaMemcpyDeviceToDevice, b->stream), "copy triplets");
+        } else {
+            memcpy(out_scores + (size_t)c * top_k, b->h_scores + (size_t)c * EPI3_MAX_TOPK,
+                   sizeof(double) * nout);
+            memcpy(out_triplets + (size_t)c * 3 * top_k, b->h_trip + (size_t)c * 3 * EPI3_MAX_TOPK,
+                   sizeof(int) * 3 * nout);
+        }
+    }
+    if (dev) CK(cudaStreamSynchronize(b->stream), "copy outputs");
+    epi3_stats& s = b->stats;
+    s = epi3_stats{};
+    int n_mma = 0;
+    for (int c = 0; c < b->n; ++c) {
+        const long long m = b->h[c]->M;
+        s.n_triplets += m * (m - 1) * (m - 2) / 6;
+        s.n_candidates += b->h_ctrls[c].n_cand;
+        s.n_rescored += b->h_ctrls[c].n_final;
+        n_mma += b->path[c] == EPI3_PATH_MMA;
+    }
+    s.path = n_mma == b->n ? EPI3_PATH_MMA : (n_mma == 0 ? EPI3_PATH_POPC8 : EPI3_PATH_AUTO);
+    s.grid = b->sm_count;
+    s.block = 448;
+    s.kernel_launches = b->n + (b->n_tiles > 0 ? 1 : 0) + (b->n - n_mma) + 3 * b->n;
+    cudaEventElapsedTime(&s.scan_kernel_ms, b->ev[1], b->ev[2]);
+    cudaEventElapsedTime(&s.select_ms, b->ev[2], b->ev[3]);
+    cudaEventElapsedTime(&s.total_ms, b->ev[0], b->ev[3]);
+    s.pack_ms = b->tune_ms;
+    return EPI3_OK;
+}
+
+int epi3_batch_destroy(epi3_batch* b) {
+    g_err.clear();
+    batch_release(b);
+    return EPI3_OK;
+}
+
+int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out) {
+    if (!b || !out) return fail(EPI3_ERR_ARG, "null argument");
+    *out = b->stats;
+    return EPI3_OK;
+}
+
+int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths) {
+    if (!b || !out_paths) return fail(EPI3_ERR_ARG, "null argument");
+    for (int c = 0; c < b->n; ++c) out_paths[c] = b->path[c];
+    return EPI3_OK;
+}
+
+int epi3_scan_batch(int32_t n_cohorts, const epi3_cohort* cohorts, int32_t top_k,
+                    int32_t* out_triplets, double* out_scores, int32_t flags, void* cuda_stream) {
+    epi3_batch* b = nullptr;
+    int rc = epi3_batch_create(&b, n_cohorts, cohorts, flags, cuda_stream);
+    if (rc != EPI3_OK) return rc;
+    rc = epi3_batch_scan(b, top_k, out_triplets, out_scores);
+    const std::string msg = g_err;
+    epi3_batch_destroy(b);
+    g_err = msg;
+    return rc;
 }
 
 }  // extern "C"

@@ -115,11 +115,26 @@ size_t scan_mma_smem();
 int mma_samples_per_step(bool fp8);
 cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
                           int kb_count, bool fp8, cudaStream_t st);
-cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTables& pt,
-                            const uint8_t* oh, long long off1, int KS0, int KS1, const int4* tiles,
-                            long long n_tiles, long long pair_begin, long long pair_end, Ctrl* ctrl,
-                            Cand* cand, long long cand_cap, int top_k, bool fp8, int grid,
-                            float* dbg, cudaStream_t st);
+// One data set ("cohort") as the tensor-core scan sees it.  The kernel reads these from
+// device memory, one per tile (tile.w = cohort index), so one launch can scan many.
+struct CohortDev {
+    Planes pl;
+    K2Tables k2;
+    PairTables pt;
+    const uint8_t* oh;        // pre-tiled one-hot A chunks
+    long long oh_off1;        // chunk index of class 1 (class 0 starts at 0)
+    int KS[2];                // K-steps per class
+    long long pair_begin, pair_end;
+    Ctrl* ctrl;
+    Cand* cand;
+    long long cand_cap;
+    int top_k;
+    float* dbg;
+};
+
+// tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
+cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
+                            bool fp8, int grid, cudaStream_t st);
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 
 // Message returned by epi3_last_error() on this thread.

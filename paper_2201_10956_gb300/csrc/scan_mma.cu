@@ -42,23 +42,6 @@ constexpr int kCandCapMma = 1024;
 constexpr int kRoundMax = 2 * kEpiThreads;   // appends per epilogue round at most
 
 
-struct MmaArgs {
-    Planes pl;
-    K2Tables k2;
-    PairTables pt;
-    const uint8_t* oh;       // pre-tiled A chunks
-    long long oh_off[2];     // chunk index of (class c, k-block 0, step 0)
-    int KS[2];               // K-steps per class
-    const int4* tiles;       // (i, jb, kb, 0)
-    long long n_tiles;
-    long long pair_begin, pair_end;   // pairs (i, j) scanned: p = j(j-1)/2 + i in [begin, end)
-    Ctrl* ctrl;
-    Cand* cand;
-    long long cand_cap;
-    int top_k;
-    float* dbg;              // optional: FP32 score of every triplet at (i*M + j)*M + k
-};
-
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -233,7 +216,7 @@ struct EpiShared {
 
 // Sort the buffer, publish this CTA's band threshold, keep the entries inside the band;
 // spill to the global list when too many tie.  Called by all epilogue threads.
-__device__ int epi_prune(const MmaArgs& a, EpiShared& es, int cnt, int tid, bool final_flush) {
+__device__ int epi_prune(const CohortDev& a, EpiShared& es, int cnt, int tid, bool final_flush) {
     const float kInf = __int_as_float(0x7f800000);
     if (cnt >= a.top_k) {
         for (int idx = cnt + tid; idx < kCandCapMma; idx += kEpiThreads) es.buf[idx].s = kInf;
@@ -278,8 +261,45 @@ __device__ int epi_prune(const MmaArgs& a, EpiShared& es, int cnt, int tid, bool
     return kept;
 }
 
+// Walks one CTA's sequence of (tile, class, K-step): tiles blockIdx.x + n * gridDim.x,
+// class 0 then class 1, K-steps of the tile's cohort (classes without samples skipped).
+struct StepCursor {
+    long long tl;
+    int c, ks, ks0, ks1;
+    int4 tile;
+    const CohortDev* cd;
+    bool valid;
+};
+
+__device__ __forceinline__ void cursor_load(StepCursor& cu, const CohortDev* cds, const int4* tiles,
+                                            long long my_tiles) {
+    cu.valid = cu.tl < my_tiles;
+    if (!cu.valid) return;
+    cu.tile = tiles[blockIdx.x + cu.tl * gridDim.x];
+    cu.cd = cds + cu.tile.w;
+    cu.ks0 = cu.cd->KS[0];
+    cu.ks1 = cu.cd->KS[1];
+    cu.c = cu.ks0 > 0 ? 0 : 1;
+    cu.ks = 0;
+}
+
+__device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds, const int4* tiles,
+                                            long long my_tiles) {
+    if (!cu.valid) return;
+    ++cu.ks;
+    if (cu.ks < (cu.c ? cu.ks1 : cu.ks0)) return;
+    if (cu.c == 0 && cu.ks1 > 0) {
+        cu.c = 1;
+        cu.ks = 0;
+        return;
+    }
+    ++cu.tl;
+    cursor_load(cu, cds, tiles, my_tiles);
+}
+
 template <bool kFp8>
-__global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) {
+__global__ void __launch_bounds__(kThreads, 1)
+scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles) {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
     uint8_t* base = reinterpret_cast<uint8_t*>(
@@ -326,39 +346,38 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int steps_per_tile = a.KS[0] + a.KS[1];
     const long long my_tiles =
-        a.n_tiles > blockIdx.x ? (a.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    const long long n_steps = my_tiles * steps_per_tile;
-    auto fail = [&]() {
+        n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    auto fail = [&](const CohortDev* cd) {
         *abort_flag = 1;
-        atomicOr(&a.ctrl->status, kStTimeout);
+        atomicOr(&cd->ctrl->status, kStTimeout);
     };
 
     if (warp == 0) {
         // ------------------------------------------------ A loader (lane 0)
         if (lane == 0) {
+            StepCursor cu{};
+            cu.tl = 0;
+            cursor_load(cu, cds, tiles, my_tiles);
             long long q = 0;
-            for (; q < n_steps; ++q) {
+            for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
                 const int s = (int)(q % kStages);
                 const unsigned ph = (unsigned)((q / kStages) & 1);
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
-                    fail();
+                    fail(cu.cd);
                     break;
                 }
-                const long long tl = q / steps_per_tile;
-                const int r = (int)(q - tl * steps_per_tile);
-                const int c = r < a.KS[0] ? 0 : 1;
-                const int ks = c ? r - a.KS[0] : r;
-                const int4 tile = a.tiles[blockIdx.x + tl * gridDim.x];
-                const long long chunk = a.oh_off[c] + (long long)tile.z * a.KS[c] + ks;
+                const long long chunk =
+                    (cu.c ? cu.cd->oh_off1 : 0) + (long long)cu.tile.z * (cu.c ? cu.ks1 : cu.ks0) + cu.ks;
                 mbar_arrive_tx(fullA0 + 8 * s, kChunk);
-                bulk_g2s(smem_u32(sA + s * kChunk), a.oh + chunk * kChunk, kChunk, fullA0 + 8 * s);
+                bulk_g2s(smem_u32(sA + s * kChunk), cu.cd->oh + chunk * kChunk, kChunk,
+                         fullA0 + 8 * s);
             }
             // drain: the copies of the last stages issued must land before the CTA exits
             for (long long d = (q > kStages ? q - kStages : 0); d < q; ++d) {
                 const int s = (int)(d % kStages);
-                mbar_wait(fullA0 + 8 * s, (unsigned)((d / kStages) & 1), abort_flag);
+                volatile int no_abort = 0;
+                mbar_wait(fullA0 + 8 * s, (unsigned)((d / kStages) & 1), &no_abort);
             }
         }
     } else if (warp == kWarpMma) {
@@ -367,20 +386,23 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
             long long q = 0;
             bool ok = true;
             for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+                const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
+                const CohortDev* cd = cds + tile.w;
+                const int KS[2] = {cd->KS[0], cd->KS[1]};
                 const int buf = (int)(tl & 1);
                 if (!mbar_wait(accE0 + 8 * buf, (unsigned)(((tl >> 1) & 1) ^ 1), abort_flag)) {
-                    fail();
+                    fail(cd);
                     break;
                 }
                 tc_fence_after();
                 for (int c = 0; c < 2 && ok; ++c) {
                     const uint32_t d = tmem + buf * 256 + c * 128;
-                    for (int ks = 0; ks < a.KS[c]; ++ks, ++q) {
+                    for (int ks = 0; ks < KS[c]; ++ks, ++q) {
                         const int s = (int)(q % kStages);
                         const unsigned ph = (unsigned)((q / kStages) & 1);
                         if (!mbar_wait(fullA0 + 8 * s, ph, abort_flag) ||
                             !mbar_wait(fullB0 + 8 * s, ph, abort_flag)) {
-                            fail();
+                            fail(cd);
                             ok = false;
                             break;
                         }
@@ -406,37 +428,41 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
         const int r = threadIdx.x - kProdWarp0 * 32;
         const int jj = r >> 2, ga = (r >> 1) & 1, gb = r & 1;
         uint4 rx[kPrefetch], ry[kPrefetch];
-        auto fetch = [&](long long q, uint4& x, uint4& y) {
-            if (q >= n_steps) return;
-            const long long tl = q / steps_per_tile;
-            const int rr = (int)(q - tl * steps_per_tile);
-            const int c = rr < a.KS[0] ? 0 : 1;
-            const int ks = c ? rr - a.KS[0] : rr;
-            const int4 tile = a.tiles[blockIdx.x + tl * gridDim.x];
-            x = step_bits<kFp8>(a.pl, c, ga, tile.x, ks);
-            y = step_bits<kFp8>(a.pl, c, gb, tile.y * kJB + jj, ks);
+        StepCursor fc{}, cc{};   // fetch cursor runs kPrefetch steps ahead of the consume cursor
+        fc.tl = 0;
+        cc.tl = 0;
+        cursor_load(fc, cds, tiles, my_tiles);
+        cursor_load(cc, cds, tiles, my_tiles);
+        auto fetch = [&](uint4& x, uint4& y) {
+            if (!fc.valid) return;
+            const Planes& pl = fc.cd->pl;
+            x = step_bits<kFp8>(pl, fc.c, ga, fc.tile.x, fc.ks);
+            y = step_bits<kFp8>(pl, fc.c, gb, fc.tile.y * kJB + jj, fc.ks);
+            cursor_next(fc, cds, tiles, my_tiles);
         };
 #pragma unroll
-        for (int u = 0; u < kPrefetch; ++u) fetch(u, rx[u], ry[u]);
+        for (int u = 0; u < kPrefetch; ++u) fetch(rx[u], ry[u]);
         bool ok = true;
-        for (long long q0 = 0; q0 < n_steps && ok; q0 += kPrefetch) {
+        long long q = 0;
+        while (cc.valid && ok) {
 #pragma unroll
             for (int u = 0; u < kPrefetch; ++u) {
-                const long long q = q0 + u;
-                if (q >= n_steps || !ok) break;
+                if (!cc.valid || !ok) break;
                 const int s = (int)(q % kStages);
                 const unsigned ph = (unsigned)((q / kStages) & 1);
                 const uint32_t w[4] = {rx[u].x & ry[u].x, rx[u].y & ry[u].y, rx[u].z & ry[u].z,
                                        rx[u].w & ry[u].w};
-                fetch(q + kPrefetch, rx[u], ry[u]);
+                fetch(rx[u], ry[u]);
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
-                    fail();
+                    fail(cc.cd);
                     ok = false;
                     break;
                 }
                 store_row<kFp8>(sB + s * kChunk, (uint32_t)r, w);
                 fence_proxy_async();
                 mbar_arrive(fullB0 + 8 * s);
+                ++q;
+                cursor_next(cc, cds, tiles, my_tiles);
             }
         }
     } else {
@@ -445,14 +471,25 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
         const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;
         const int L = quad * 32 + lane;                 // TMEM lane = A row = (kk, z)
         const int kk = L >> 1, z = L & 1;
-        const int M = a.pl.M;
-        int cnt = 0;
+        int cnt = 0, cur = -1;
         bool ok = true;
         for (long long tl = 0; tl < my_tiles && ok; ++tl) {
             const int buf = (int)(tl & 1);
-            const int4 tile = a.tiles[blockIdx.x + tl * gridDim.x];
+            const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
+            const CohortDev& cd = cds[tile.w];
+            if (tile.w != cur) {  // candidates are per cohort: flush the previous one's
+                if (cur >= 0) cnt = epi_prune(cds[cur], es, cnt, tid, true);
+                if (tid == 0) {
+                    es.cnt = 0;
+                    es.tloc = __int_as_float(0x7f800000);
+                }
+                epi_bar();
+                cnt = 0;
+                cur = tile.w;
+            }
+            const int M = cd.pl.M;
             const int i = tile.x, j0 = tile.y * kJB, k = tile.z * kKB + kk;
-            if (!mbar_wait(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag)) fail();
+            if (!mbar_wait(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag)) fail(&cd);
             epi_bar();  // uniform decision: every epilogue thread stops on the same tile
             if (tid == 0) es.stop = *abort_flag;
             epi_bar();
@@ -461,17 +498,19 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
                 break;
             }
             tc_fence_after();
+            const int KS0 = cd.KS[0], KS1 = cd.KS[1];
+            const PairTables pt = cd.pt;
             const bool krow = (k < M) && (k > i);
             int4 pxz[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
             int2 mz[2] = {make_int2(0, 0), make_int2(0, 0)}, mx[2];
             if (krow) {
-                pxz[0] = __ldg(a.pt.pt + pair_index(i, k));
-                pxz[1] = __ldg(a.pt.pt + a.pt.n_pairs + pair_index(i, k));
-                mz[0] = __ldg(a.pt.marg + k);
-                mz[1] = __ldg(a.pt.marg + M + k);
+                pxz[0] = __ldg(pt.pt + pair_index(i, k));
+                pxz[1] = __ldg(pt.pt + pt.n_pairs + pair_index(i, k));
+                mz[0] = __ldg(pt.marg + k);
+                mz[1] = __ldg(pt.marg + M + k);
             }
-            mx[0] = __ldg(a.pt.marg + i);
-            mx[1] = __ldg(a.pt.marg + M + i);
+            mx[0] = __ldg(pt.marg + i);
+            mx[1] = __ldg(pt.marg + M + i);
             for (int gi = 0; gi < 4; ++gi) {
                 const int g = half + 2 * gi;            // 16-column group = 4 second SNPs
                 uint32_t v[2][16];
@@ -482,10 +521,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
                 tc_wait_ld();
                 int cv[2][16];
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int t = 0; t < 16; ++t)
-                        cv[c][t] = a.KS[c] ? __float2int_rn(__uint_as_float(v[c][t])) : 0;
+                for (int t = 0; t < 16; ++t) {
+                    cv[0][t] = KS0 ? __float2int_rn(__uint_as_float(v[0][t])) : 0;
+                    cv[1][t] = KS1 ? __float2int_rn(__uint_as_float(v[1][t])) : 0;
+                }
                 // my triplets: jj = 4g + z + 2m; the partner lane (other z) holds the
                 // other third-SNP genotype of the same (k, jj): swap what each one needs.
                 int got[2][8];
@@ -503,36 +542,34 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
                     const int j = j0 + jj;
                     if (!(krow && j > i && j < k)) continue;
                     const long long pij = pair_index(i, j);
-                    if (pij < a.pair_begin || pij >= a.pair_end) continue;
+                    if (pij < cd.pair_begin || pij >= cd.pair_end) continue;
                     int r0[kCells], r1[kCells];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         int n8[8];
 #pragma unroll
                         for (int ab = 0; ab < 4; ++ab) {
-                            const int mine = cv[c][(z + 2 * m) * 4 + ab];
-                            const int other = got[c][4 * m + ab];
-                            n8[2 * ab + z] = mine;       // n8[4a + 2b + gz], ab = 2a + b
-                            n8[2 * ab + (1 - z)] = other;
+                            n8[2 * ab + z] = cv[c][(z + 2 * m) * 4 + ab];  // n8[4a + 2b + gz]
+                            n8[2 * ab + (1 - z)] = got[c][4 * m + ab];
                         }
-                        derive27(n8, __ldg(a.pt.pt + c * a.pt.n_pairs + pair_index(i, j)), pxz[c],
-                                 __ldg(a.pt.pt + c * a.pt.n_pairs + pair_index(j, k)), mx[c],
-                                 __ldg(a.pt.marg + (size_t)c * M + j), mz[c], a.pt.n_c[c],
+                        derive27(n8, __ldg(pt.pt + c * pt.n_pairs + pij), pxz[c],
+                                 __ldg(pt.pt + c * pt.n_pairs + pair_index(j, k)), mx[c],
+                                 __ldg(pt.marg + (size_t)c * M + j), mz[c], pt.n_c[c],
                                  c ? r1 : r0);
                     }
                     // guard the log-factorial lookups: every cell must lie in [0, N_c]
                     bool sane = true;
 #pragma unroll
                     for (int q = 0; q < kCells; ++q)
-                        sane &= (unsigned)r0[q] <= (unsigned)a.pt.n_c[0] &&
-                                (unsigned)r1[q] <= (unsigned)a.pt.n_c[1];
+                        sane &= (unsigned)r0[q] <= (unsigned)pt.n_c[0] &&
+                                (unsigned)r1[q] <= (unsigned)pt.n_c[1];
                     if (!sane) {
-                        atomicOr(&a.ctrl->status, kStBadCount);
+                        atomicOr(&cd.ctrl->status, kStBadCount);
                         continue;
                     }
-                    const float s = k2_f32(r0, r1, a.k2.lf2);
-                    if (a.dbg) a.dbg[((size_t)i * M + j) * M + k] = s;
-                    if (s <= fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr))) {
+                    const float s = k2_f32(r0, r1, cd.k2.lf2);
+                    if (cd.dbg) cd.dbg[((size_t)i * M + j) * M + k] = s;
+                    if (s <= fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&cd.ctrl->thr))) {
                         const int idx = atomicAdd(&es.cnt, 1);
                         es.buf[idx] = Cand{s, i, j, k};
                     }
@@ -541,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
                 cnt = es.cnt;
                 epi_bar();
                 if (cnt > kCandCapMma - kRoundMax) {
-                    cnt = epi_prune(a, es, cnt, tid, false);
+                    cnt = epi_prune(cd, es, cnt, tid, false);
                     if (tid == 0) es.cnt = cnt;
                     epi_bar();
                 }
@@ -550,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_mma_kernel(const MmaArgs a) 
             __syncwarp();
             if (lane == 0) mbar_arrive(accE0 + 8 * buf);
         }
-        epi_prune(a, es, cnt, tid, true);
+        if (cur >= 0) epi_prune(cds[cur], es, cnt, tid, true);
     }
     __syncthreads();
     if (warp == 0) {
@@ -607,41 +644,20 @@ cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_mma(const Planes& pl, const K2Tables& k2, const PairTables& pt,
-                            const uint8_t* oh, long long off1, int KS0, int KS1, const int4* tiles,
-                            long long n_tiles, long long pair_begin, long long pair_end, Ctrl* ctrl,
-                            Cand* cand, long long cand_cap, int top_k, bool fp8, int grid,
-                            float* dbg, cudaStream_t st) {
-    MmaArgs a;
-    a.pl = pl;
-    a.k2 = k2;
-    a.pt = pt;
-    a.oh = oh;
-    a.oh_off[0] = 0;
-    a.oh_off[1] = off1;
-    a.KS[0] = KS0;
-    a.KS[1] = KS1;
-    a.tiles = tiles;
-    a.n_tiles = n_tiles;
-    a.pair_begin = pair_begin;
-    a.pair_end = pair_end;
-    a.ctrl = ctrl;
-    a.cand = cand;
-    a.cand_cap = cand_cap;
-    a.top_k = top_k;
-    a.dbg = dbg;
+cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
+                            bool fp8, int grid, cudaStream_t st) {
     const size_t smem = scan_mma_smem();
     cudaError_t e;
     if (fp8) {
         e = cudaFuncSetAttribute(scan_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        scan_mma_kernel<true><<<grid, kThreads, smem, st>>>(a);
+        scan_mma_kernel<true><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles);
     } else {
         e = cudaFuncSetAttribute(scan_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        scan_mma_kernel<false><<<grid, kThreads, smem, st>>>(a);
+        scan_mma_kernel<false><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles);
     }
     return cudaGetLastError();
 }

@@ -27,13 +27,19 @@ MAX_TOPK = 512
 # Every symbol the header declares; tests check the library exports all of them.
 SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_destroy", "epi3_last_error",
            "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
-           "epi3_scan_noalloc", "epi3_scan_scores")
+           "epi3_scan_noalloc", "epi3_scan_scores", "epi3_batch_create", "epi3_batch_scan",
+           "epi3_batch_destroy", "epi3_batch_get_stats", "epi3_batch_get_paths", "epi3_scan_batch")
 
 
 class Epi3Error(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"epi3 error {code}: {msg}")
         self.code = code
+
+
+class Cohort(ctypes.Structure):
+    _fields_ = [("genotypes", ctypes.c_void_p), ("phenotype", ctypes.c_void_p),
+                ("n_snps", ctypes.c_int32), ("n_samples", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -72,6 +78,12 @@ def load(path: str = LIB_PATH):
                            ctypes.POINTER(I32)],
         "epi3_scan_noalloc": [P, P, I32, I32, I32, P, P, P],
         "epi3_scan_scores": [P, I32, P],
+        "epi3_batch_create": [ctypes.POINTER(P), I32, P, I32, P],
+        "epi3_batch_scan": [P, I32, P, P],
+        "epi3_batch_destroy": [P],
+        "epi3_batch_get_stats": [P, ctypes.POINTER(Stats)],
+        "epi3_batch_get_paths": [P, P],
+        "epi3_scan_batch": [I32, P, I32, P, P, I32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -219,6 +231,95 @@ class Handle:
         v = [ctypes.c_int32() for _ in range(4)]
         _check(load().epi3_get_shape(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+
+class Batch:
+    """Many cohorts scanned together (epi3_batch_*): one persistent tensor-core launch for
+    the cohorts the tuner gives to it, everything replayed from one CUDA graph.
+
+    datasets: list of (genotypes [M, N], phenotype [N]) pairs, all numpy (host) or all CUDA
+    torch tensors (device)."""
+
+    def __init__(self, datasets, stream=None):
+        lib = load()
+        self._dev = _is_torch(datasets[0][0])
+        keep, arr = [], (Cohort * len(datasets))()
+        for c, (g, p) in enumerate(datasets):
+            if self._dev:
+                import torch
+                g = g.contiguous().to(torch.uint8)
+                p = p.contiguous().to(torch.uint8)
+            else:
+                g = np.ascontiguousarray(g, dtype=np.uint8)
+                p = np.ascontiguousarray(p, dtype=np.uint8)
+            keep.append((g, p))
+            arr[c] = Cohort(_ptr(g).value, _ptr(p).value, int(g.shape[0]), int(g.shape[1]))
+        sptr = None
+        if stream is not None:
+            sptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        elif self._dev:
+            import torch
+            sptr = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        b = ctypes.c_void_p()
+        _check(lib.epi3_batch_create(ctypes.byref(b), len(datasets), ctypes.cast(arr, ctypes.c_void_p),
+                                     DEVICE_PTRS if self._dev else 0, sptr))
+        self._b = b
+        self.n = len(datasets)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().epi3_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def scan(self, top_k: int):
+        """Per cohort top-k: triplets [n, k, 3] int32, FP64 K2 [n, k]."""
+        if self._dev:
+            import torch
+            trip = torch.empty((self.n, top_k, 3), dtype=torch.int32, device="cuda")
+            sc = torch.empty((self.n, top_k), dtype=torch.float64, device="cuda")
+        else:
+            trip = np.empty((self.n, top_k, 3), dtype=np.int32)
+            sc = np.empty((self.n, top_k), dtype=np.float64)
+        _check(load().epi3_batch_scan(self._b, int(top_k), _ptr(trip), _ptr(sc)))
+        return trip, sc
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().epi3_batch_get_stats(self._b, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def paths(self):
+        out = np.empty(self.n, dtype=np.int32)
+        _check(load().epi3_batch_get_paths(self._b, _ptr(out)))
+        return out
+
+
+def scan_batch(datasets, top_k: int):
+    """One-shot epi3_scan_batch on host (numpy) inputs."""
+    lib = load()
+    keep, arr = [], (Cohort * len(datasets))()
+    for c, (g, p) in enumerate(datasets):
+        g = np.ascontiguousarray(g, dtype=np.uint8)
+        p = np.ascontiguousarray(p, dtype=np.uint8)
+        keep.append((g, p))
+        arr[c] = Cohort(_ptr(g).value, _ptr(p).value, int(g.shape[0]), int(g.shape[1]))
+    trip = np.empty((len(datasets), top_k, 3), dtype=np.int32)
+    sc = np.empty((len(datasets), top_k), dtype=np.float64)
+    _check(lib.epi3_scan_batch(len(datasets), ctypes.cast(arr, ctypes.c_void_p), int(top_k),
+                               _ptr(trip), _ptr(sc), 0, None))
+    return trip, sc
 
 
 def scan_noalloc(genotypes, phenotype, top_k: int, stream=None):
