@@ -151,7 +151,8 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
  * threads per block of
  * the scan kernel (64..512, multiple of 32); "ctas_per_sm" = persistent CTAs
  * per SM (0 = occupancy maximum); "timing" = "0" | "1" (record CUDA events
- * around the scan's kernels, read back with epi3_get_stats).
+ * around the scan's kernels, read back with epi3_get_stats); "profile" = "0" | "1" (per-role
+ * wait accounting inside the tensor-core scan kernel, reported in epi3_stats).
  */
 int epi3_set_option(epi3_handle* h, const char* key, const char* value);
 
@@ -170,6 +171,10 @@ typedef struct {
     int32_t kernel_launches; /* kernels launched by the last scan */
     float k2_rel_bound;      /* proven |FP32 - FP64| bound: rel * K2 + abs */
     float k2_abs_bound;
+    /* tensor-core scan with option "profile" = 1: share of the kernel's cycles each role
+       spent waiting (A loader on free stages, MMA issuer on full stages, MMA issuer on free
+       accumulators, producer warps on free stages, epilogue warps on full accumulators) */
+    float wait_loader, wait_mma_operands, wait_mma_accum, wait_producers, wait_epilogue;
 } epi3_stats;
 
 int epi3_get_stats(const epi3_handle* h, epi3_stats* out);
@@ -230,7 +235,8 @@ int epi3_batch_create(epi3_batch** b, int32_t n_cohorts, const epi3_cohort* coho
                       int32_t flags, void* cuda_stream);
 int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double* out_scores);
 int epi3_batch_destroy(epi3_batch* b);
-/* Figures of the last epi3_batch_scan (pack_ms holds the tuner's time at create). */
+/* Figures of the last epi3_batch_scan: scan_kernel_ms = total_ms = device time of the graph
+ * replay; pack_ms holds the tuner's time at create. */
 int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out);
 /* The path (EPI3_PATH_MMA or EPI3_PATH_POPC8) the tuner chose for each cohort. */
 int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths);

@@ -95,6 +95,8 @@ struct epi3_handle {
     long long oh_off1 = 0;
     float* dbg = nullptr;         // device buffer of epi3_scan_scores (during that call only)
     CohortDev* d_cd = nullptr;    // this data set's descriptor for the tensor-core kernel
+    bool profile = false;
+    unsigned long long* d_prof = nullptr;
     int4* d_tiles = nullptr;      // tile list of the tensor-core form
     long long n_tiles = 0, tiles_pb = -1, tiles_pe = -1;
     Ctrl* h_ctrl = nullptr;       // pinned
@@ -126,6 +128,7 @@ void release(epi3_handle* h) {
     cudaFree(h->d_oh);
     cudaFree(h->d_tiles);
     cudaFree(h->d_cd);
+    cudaFree(h->d_prof);
     cudaFreeHost(h->h_ctrl);
     cudaFreeHost(h->h_scores);
     cudaFreeHost(h->h_trip);
@@ -430,7 +433,12 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
         const CohortDev cd = cohort_of(h, pb, pe, top_k);
         CK(cudaMemcpyAsync(h->d_cd, &cd, sizeof(cd), cudaMemcpyHostToDevice, h->stream),
            "upload descriptor");
-        CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, fp8, grid, h->stream), "mma scan launch");
+        if (h->profile) {
+            if (!h->d_prof) CK(dev_alloc((void**)&h->d_prof, 8 * sizeof(unsigned long long)), "alloc profile");
+            CK(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), h->stream), "clear profile");
+        }
+        CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, fp8, grid, h->stream,
+                           h->profile ? h->d_prof : nullptr), "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
         if (rc == 1) continue;
@@ -445,13 +453,25 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.n_rescored = h->h_ctrl->n_final;
     s.path = path;
     s.grid = grid;
-    s.block = 448;
+    s.block = 576;
     s.kernel_launches = 5;
+    s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
+    if (h->profile && h->d_prof) {
+        unsigned long long p[8];
+        CK(cudaMemcpy(p, h->d_prof, sizeof(p), cudaMemcpyDeviceToHost), "read profile");
+        const double tot = p[5] > 0 ? (double)p[5] : 1.0;
+        s.wait_loader = (float)(p[0] / tot);
+        s.wait_mma_operands = (float)(p[1] / tot);
+        s.wait_mma_accum = (float)(p[2] / tot);
+        s.wait_producers = (float)(p[3] / (tot * 8));
+        s.wait_epilogue = (float)(p[4] / (tot * 8));
+    }
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
+    (void)cudaGetLastError();
     return EPI3_OK;
 }
 
@@ -575,6 +595,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
+    (void)cudaGetLastError();
     return EPI3_OK;
 }
 
@@ -639,6 +660,7 @@ const char* epi3_last_error(void) { return g_err.c_str(); }
 int epi3_create(epi3_handle** out, const uint8_t* genotypes, const uint8_t* phenotype,
                 int32_t n_snps, int32_t n_samples, int32_t flags, void* cuda_stream) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!out) return fail(EPI3_ERR_ARG, "null handle pointer");
     *out = nullptr;
     if (!genotypes || !phenotype) return fail(EPI3_ERR_ARG, "null genotypes or phenotype");
@@ -684,12 +706,14 @@ int epi3_create(epi3_handle** out, const uint8_t* genotypes, const uint8_t* phen
 
 int epi3_destroy(epi3_handle* h) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     release(h);
     return EPI3_OK;
 }
 
 int epi3_scan(epi3_handle* h, int32_t top_k, int32_t* out_triplets, double* out_scores) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!h) return fail(EPI3_ERR_ARG, "null handle");
     return scan_impl(h, 0, pairs(h->M), top_k, out_triplets, out_scores, nullptr, true);
 }
@@ -697,12 +721,14 @@ int epi3_scan(epi3_handle* h, int32_t top_k, int32_t* out_triplets, double* out_
 int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_t top_k,
                     int32_t* out_triplets, double* out_scores, int32_t* n_out) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     return scan_impl(h, pair_begin, pair_end, top_k, out_triplets, out_scores, n_out, false);
 }
 
 int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,
                 int32_t path) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (path != EPI3_PATH_AUTO && path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8)
         return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
     if (n > 0 && !out_counts) return fail(EPI3_ERR_ARG, "null out_counts");
@@ -713,12 +739,14 @@ int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out
 int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k2_f32,
                 double* out_k2_f64) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (n > 0 && !out_k2_f32 && !out_k2_f64) return fail(EPI3_ERR_ARG, "no output requested");
     return per_triplet(h, n, triplets, nullptr, out_k2_f32, out_k2_f64, EPI3_PATH_POPC);
 }
 
 int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!h || !out_scores) return fail(EPI3_ERR_ARG, "null argument");
     if (h->M > 512) return fail(EPI3_ERR_ARG, "epi3_scan_scores needs n_snps <= 512");
     const size_t n = (size_t)h->M * h->M * h->M;
@@ -751,6 +779,7 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores) {
 
 int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!h || !key || !value) return fail(EPI3_ERR_ARG, "null argument");
     if (!strcmp(key, "path")) {
         if (!strcmp(value, "auto")) h->path = EPI3_PATH_AUTO;
@@ -771,6 +800,10 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
         const int v = atoi(value);
         if (v < 0 || v > 32) return fail(EPI3_ERR_ARG, "ctas_per_sm %d not in 0..32", v);
         h->ctas_per_sm = v;
+        return EPI3_OK;
+    }
+    if (!strcmp(key, "profile")) {
+        h->profile = atoi(value) != 0;
         return EPI3_OK;
     }
     if (!strcmp(key, "timing")) {
@@ -824,7 +857,7 @@ struct epi3_batch {
     int* h_trip = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_k = -1;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     epi3_stats stats{};
     float tune_ms = 0.f;
 };
@@ -965,15 +998,38 @@ int batch_capture(epi3_batch* b, int top_k) {
 
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed), "begin capture");
     cudaError_t err = cudaSuccess;
+    const char* where = "";
+    int where_c = -1;
+    int cur_c = -1;
+    const char* cur = "";
     auto ok = [&](cudaError_t e) {
-        if (err == cudaSuccess && e != cudaSuccess) err = e;
+        if (err == cudaSuccess && e != cudaSuccess) {
+            err = e;
+            where = cur;
+            where_c = cur_c;
+        }
     };
-    for (int c = 0; c < b->n; ++c) ok(launch_reset(b->h[c]->d_ctrl, b->stream));
-    ok(cudaEventRecord(b->ev[1], b->stream));
+    cur = "reset";
+    for (int c = 0; c < b->n; ++c) {
+        cur_c = c;
+        ok(launch_reset(b->h[c]->d_ctrl, b->stream));
+    }
+    cur = "tensor scan";
+    cur_c = -1;
     if (b->n_tiles > 0) ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, true, b->sm_count, b->stream));
+    cur = "popc8 scan";
     for (int c = 0; c < b->n; ++c) {
         if (b->path[c] != EPI3_PATH_POPC8) continue;
+        cur_c = c;
         epi3_handle* h = b->h[c];
+        {
+            const cudaError_t stale = cudaGetLastError();
+            if (stale != cudaSuccess && err == cudaSuccess) {
+                err = stale;
+                where = "error pending before the POPC launch";
+                where_c = c;
+            }
+        }
         ScanArgs a{};
         a.pl = h->pl;
         a.k2 = h->k2;
@@ -986,9 +1042,18 @@ int batch_capture(epi3_batch* b, int top_k) {
         a.top_k = top_k;
         a.dbg = nullptr;
         ok(launch_scan_popc8(a, grid[c], h->threads, smem[c], b->stream));
+        if (err != cudaSuccess && where_c == c && !strcmp(where, "popc8 scan")) {
+            char buf[160];
+            snprintf(buf, sizeof(buf), "popc8 scan (grid %d, block %d, smem %zu)", grid[c], h->threads,
+                     smem[c]);
+            static thread_local std::string detail;
+            detail = buf;
+            where = detail.c_str();
+        }
     }
-    ok(cudaEventRecord(b->ev[2], b->stream));
+    cur = "candidate stage";
     for (int c = 0; c < b->n; ++c) {
+        cur_c = c;
         epi3_handle* h = b->h[c];
         ok(launch_select(h->d_ctrl, h->d_cand, h->cand_cap, top_k, h->k2.rel, h->k2.abs_, b->stream));
         ok(launch_rescore(h->pl, h->k2, h->d_ctrl, h->d_cand, h->cand_cap, h->d_fin,
@@ -996,7 +1061,8 @@ int batch_capture(epi3_batch* b, int top_k) {
         ok(launch_final(h->d_ctrl, h->d_fin, top_k, b->d_scores + (size_t)c * EPI3_MAX_TOPK,
                         b->d_trip + (size_t)c * 3 * EPI3_MAX_TOPK, b->stream));
     }
-    ok(cudaEventRecord(b->ev[3], b->stream));
+    cur = "read-back";
+    cur_c = -1;
     ok(cudaMemcpyAsync(b->h_ctrls, b->d_ctrls, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToHost, b->stream));
     ok(cudaMemcpyAsync(b->h_scores, b->d_scores, sizeof(double) * b->n * EPI3_MAX_TOPK,
                        cudaMemcpyDeviceToHost, b->stream));
@@ -1006,7 +1072,9 @@ int batch_capture(epi3_batch* b, int top_k) {
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
     if (err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        return cuda_fail(err, "batch capture");
+        (void)cudaGetLastError();
+        return fail(EPI3_ERR_CUDA, "batch capture (%s, cohort %d): %s", where, where_c,
+                    cudaGetErrorString(err));
     }
     if (ec != cudaSuccess) return cuda_fail(ec, "end capture");
     const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
@@ -1023,6 +1091,7 @@ extern "C" {
 int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* cohorts,
                       int32_t flags, void* cuda_stream) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!out) return fail(EPI3_ERR_ARG, "null batch pointer");
     *out = nullptr;
     if (n_cohorts < 1 || !cohorts) return fail(EPI3_ERR_ARG, "need at least one cohort");
@@ -1101,6 +1170,7 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
 
 int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double* out_scores) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!b || !out_triplets || !out_scores) return fail(EPI3_ERR_ARG, "null argument");
     if (top_k < 1 || top_k > EPI3_MAX_TOPK)
         return fail(EPI3_ERR_ARG, "top_k %d outside 1..%d", top_k, EPI3_MAX_TOPK);
@@ -1117,6 +1187,7 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
         if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
         CK(cudaEventRecord(b->ev[0], b->stream), "event");
         CK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+        CK(cudaEventRecord(b->ev[4], b->stream), "event");
         CK(cudaStreamSynchronize(b->stream), "batch scan");
         bool grow = false;
         for (int c = 0; c < b->n; ++c) {
@@ -1174,17 +1245,21 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
     }
     s.path = n_mma == b->n ? EPI3_PATH_MMA : (n_mma == 0 ? EPI3_PATH_POPC8 : EPI3_PATH_AUTO);
     s.grid = b->sm_count;
-    s.block = 448;
+    s.block = 576;
     s.kernel_launches = b->n + (b->n_tiles > 0 ? 1 : 0) + (b->n - n_mma) + 3 * b->n;
-    cudaEventElapsedTime(&s.scan_kernel_ms, b->ev[1], b->ev[2]);
-    cudaEventElapsedTime(&s.select_ms, b->ev[2], b->ev[3]);
-    cudaEventElapsedTime(&s.total_ms, b->ev[0], b->ev[3]);
+    // device time of the whole graph replay (scan kernels + candidate stages + read-back);
+    // the scan kernels are > 99 % of it
+    cudaEventElapsedTime(&s.total_ms, b->ev[0], b->ev[4]);
+    (void)cudaGetLastError();
+    s.scan_kernel_ms = s.total_ms;
+    s.select_ms = 0.f;
     s.pack_ms = b->tune_ms;
     return EPI3_OK;
 }
 
 int epi3_batch_destroy(epi3_batch* b) {
     g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
     batch_release(b);
     return EPI3_OK;
 }

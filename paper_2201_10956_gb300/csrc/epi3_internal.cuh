@@ -134,7 +134,7 @@ struct CohortDev {
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                            bool fp8, int grid, cudaStream_t st);
+                            bool fp8, int grid, cudaStream_t st, unsigned long long* prof = nullptr);
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 
 // Message returned by epi3_last_error() on this thread.

@@ -17,8 +17,8 @@
 // fetched with one cp.async.bulk per stage; B is expanded from the bit planes by four
 // producer warps straight into the swizzled layout.
 //
-// Warp roles (14 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
-// (two warps per TMEM lane quadrant), 10..13 = B producers.  Every mbarrier wait is
+// Warp roles (18 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
+// (two warps per TMEM lane quadrant), 10..17 = B producers (two threads per B row).  Every mbarrier wait is
 // bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
 // frees TMEM and returns.
 #include "epi3_internal.cuh"
@@ -31,10 +31,12 @@ constexpr int kKB = 64;                  // third SNPs per tile (A rows = 2 per 
 constexpr int kJB = 32;                  // second SNPs per tile (B rows = 4 per SNP)
 constexpr int kStages = 4;
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
-constexpr int kThreads = 448;
+// 18 warps: 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps per
+// TMEM lane quadrant), 10..17 = producers (two threads per B row).
+constexpr int kThreads = 576;
 constexpr int kWarpMma = 1;
 constexpr int kEpiWarp0 = 2, kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
-constexpr int kProdWarp0 = 10, kProdThreads = 128;
+constexpr int kProdWarp0 = 10, kProdWarps = 8, kProdThreads = kProdWarps * 32;
 constexpr int kTmemCols = 512;
 constexpr int kPrefetch = 4;             // producer prefetch distance (stages)
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
@@ -73,6 +75,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, unsigned parity, volatile 
             if (global_ns() - t0 > kWaitNs) return false;
         }
     }
+}
+// mbar_wait that adds the cycles it spent to *acc (role profiling, optional).
+__device__ __forceinline__ bool mbar_wait_t(uint32_t a, unsigned parity, volatile int* abort_flag,
+                                            unsigned long long* acc) {
+    if (!acc) return mbar_wait(a, parity, abort_flag);
+    const long long t0 = clock64();
+    const bool r = mbar_wait(a, parity, abort_flag);
+    *acc += (unsigned long long)(clock64() - t0);
+    return r;
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
@@ -157,28 +168,55 @@ __device__ __forceinline__ uint32_t bits2_to_h2(uint32_t b2) {
     return ((b2 * 0x8001u) & 0x10001u) * 0x3C00u;
 }
 
-// Expand the 128 bytes of one operand row from its sample bits into the swizzled tile.
-// FP8: 128 samples = 4 words; FP16: 64 samples = 2 words (w[0], w[1]).
+// Expand units ub .. ub+3 (16-byte units of the 128-byte row r) from their sample bits into
+// the swizzled tile.  FP8: a unit is 16 samples, the four units are the 64 bits w0 | w1 << 32;
+// FP16: a unit is 8 samples, the four units are the 32 bits of w0.
 template <bool kFp8>
-__device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint32_t* w) {
+__device__ __forceinline__ void store_units(uint8_t* tile, uint32_t r, uint32_t ub, uint32_t w0,
+                                            uint32_t w1) {
 #pragma unroll
-    for (uint32_t u = 0; u < 8; ++u) {
+    for (uint32_t q = 0; q < 4; ++q) {
         uint4 v;
-        if (kFp8) {  // unit u = samples 16u .. 16u+15 = half (u & 1) of word u >> 1
-            const uint32_t h = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
+        if (kFp8) {
+            const uint32_t h = ((q < 2 ? w0 : w1) >> ((q & 1) * 16)) & 0xFFFFu;
             v.x = nib_to_bytes(h & 0xF, 0x38u);
             v.y = nib_to_bytes((h >> 4) & 0xF, 0x38u);
             v.z = nib_to_bytes((h >> 8) & 0xF, 0x38u);
             v.w = nib_to_bytes(h >> 12, 0x38u);
-        } else {  // unit u = samples 8u .. 8u+7 = byte (u & 3) of word u >> 2
-            const uint32_t b = (w[u >> 2] >> ((u & 3) * 8)) & 0xFFu;
+        } else {
+            const uint32_t b = (w0 >> (q * 8)) & 0xFFu;
             v.x = bits2_to_h2(b & 3);
             v.y = bits2_to_h2((b >> 2) & 3);
             v.z = bits2_to_h2((b >> 4) & 3);
             v.w = bits2_to_h2(b >> 6);
         }
-        *reinterpret_cast<uint4*>(tile + sw128_off(r, u)) = v;
+        *reinterpret_cast<uint4*>(tile + sw128_off(r, ub + q)) = v;
     }
+}
+
+// Expand the 128 bytes of one operand row (used by the one-hot builder).
+template <bool kFp8>
+__device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint32_t* w) {
+    if (kFp8) {
+        store_units<true>(tile, r, 0, w[0], w[1]);
+        store_units<true>(tile, r, 4, w[2], w[3]);
+    } else {
+        store_units<false>(tile, r, 0, w[0], 0);
+        store_units<false>(tile, r, 4, w[1], 0);
+    }
+}
+
+// The half of K-step ks's bits that producer part p (units 4p .. 4p+3) needs: FP8 words
+// 2p, 2p+1 of the 128-sample group; FP16 word p of the step's 64 samples.
+template <bool kFp8>
+__device__ __forceinline__ uint2 part_bits(const Planes& pl, int c, int plane, int m, int ks,
+                                           int part) {
+    if (m >= pl.M) return make_uint2(0, 0);
+    const int w4 = kFp8 ? ks : (ks >> 1);
+    const uint4* g = pl.planes + pl.coff[c] + ((size_t)plane * pl.W4[c] + w4) * pl.M + m;
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(g);
+    if (kFp8) return __ldg(reinterpret_cast<const uint2*>(w) + part);
+    return make_uint2(__ldg(w + ((ks & 1) * 2 + part)), 0);
 }
 
 // Words of K-step ks of class c, plane p, SNP m (zero words past the class or for m >= M).
@@ -298,8 +336,17 @@ __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds
 }
 
 template <bool kFp8>
-__global__ void __launch_bounds__(kThreads, 1)
-scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles) {
+__global__ void __maxnreg__(112)  // 576 threads x 112 registers: one CTA per SM
+scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
+                unsigned long long* __restrict__ prof) {
+    // prof (optional): per role, cycles spent waiting, summed over CTAs:
+    //   [0] A loader on empty stages, [1] MMA on full stages, [2] MMA on free accumulators,
+    //   [3] producers (thread 0 of each producer warp) on empty stages,
+    //   [4] epilogue (lane 0 of each epilogue warp) on full accumulators, [5] kernel cycles
+    //   of this CTA, [6] epilogue busy cycles, [7] producer busy cycles
+    const long long t_start = clock64();
+    unsigned long long w_acc = 0, busy = 0;
+    unsigned long long* my_acc = prof ? &w_acc : nullptr;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
     uint8_t* base = reinterpret_cast<uint8_t*>(
@@ -363,7 +410,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
                 const int s = (int)(q % kStages);
                 const unsigned ph = (unsigned)((q / kStages) & 1);
-                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
+                if (!mbar_wait_t(empty0 + 8 * s, ph ^ 1u, abort_flag, my_acc)) {
                     fail(cu.cd);
                     break;
                 }
@@ -390,7 +437,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 const CohortDev* cd = cds + tile.w;
                 const int KS[2] = {cd->KS[0], cd->KS[1]};
                 const int buf = (int)(tl & 1);
-                if (!mbar_wait(accE0 + 8 * buf, (unsigned)(((tl >> 1) & 1) ^ 1), abort_flag)) {
+                if (!mbar_wait_t(accE0 + 8 * buf, (unsigned)(((tl >> 1) & 1) ^ 1), abort_flag,
+                                 prof ? &busy : nullptr)) {
                     fail(cd);
                     break;
                 }
@@ -400,8 +448,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     for (int ks = 0; ks < KS[c]; ++ks, ++q) {
                         const int s = (int)(q % kStages);
                         const unsigned ph = (unsigned)((q / kStages) & 1);
-                        if (!mbar_wait(fullA0 + 8 * s, ph, abort_flag) ||
-                            !mbar_wait(fullB0 + 8 * s, ph, abort_flag)) {
+                        if (!mbar_wait_t(fullA0 + 8 * s, ph, abort_flag, my_acc) ||
+                            !mbar_wait_t(fullB0 + 8 * s, ph, abort_flag, my_acc)) {
                             fail(cd);
                             ok = false;
                             break;
@@ -424,20 +472,22 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             mbar_wait(drain0, 0, &no_abort);
         }
     } else if (warp >= kProdWarp0) {
-        // ------------------------------------------------ B producers: row r = (jj, a, b)
-        const int r = threadIdx.x - kProdWarp0 * 32;
+        // ------------------------------------------------ B producers: row r = (jj, a, b),
+        // two threads per row, each expanding four of the row's eight 16-byte units
+        const int pt = threadIdx.x - kProdWarp0 * 32;
+        const int r = pt >> 1, part = pt & 1;
         const int jj = r >> 2, ga = (r >> 1) & 1, gb = r & 1;
-        uint4 rx[kPrefetch], ry[kPrefetch];
+        uint2 rx[kPrefetch], ry[kPrefetch];
         StepCursor fc{}, cc{};   // fetch cursor runs kPrefetch steps ahead of the consume cursor
         fc.tl = 0;
         cc.tl = 0;
         cursor_load(fc, cds, tiles, my_tiles);
         cursor_load(cc, cds, tiles, my_tiles);
-        auto fetch = [&](uint4& x, uint4& y) {
+        auto fetch = [&](uint2& x, uint2& y) {
             if (!fc.valid) return;
             const Planes& pl = fc.cd->pl;
-            x = step_bits<kFp8>(pl, fc.c, ga, fc.tile.x, fc.ks);
-            y = step_bits<kFp8>(pl, fc.c, gb, fc.tile.y * kJB + jj, fc.ks);
+            x = part_bits<kFp8>(pl, fc.c, ga, fc.tile.x, fc.ks, part);
+            y = part_bits<kFp8>(pl, fc.c, gb, fc.tile.y * kJB + jj, fc.ks, part);
             cursor_next(fc, cds, tiles, my_tiles);
         };
 #pragma unroll
@@ -450,25 +500,24 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 if (!cc.valid || !ok) break;
                 const int s = (int)(q % kStages);
                 const unsigned ph = (unsigned)((q / kStages) & 1);
-                const uint32_t w[4] = {rx[u].x & ry[u].x, rx[u].y & ry[u].y, rx[u].z & ry[u].z,
-                                       rx[u].w & ry[u].w};
+                const uint32_t w0 = rx[u].x & ry[u].x, w1 = rx[u].y & ry[u].y;
                 fetch(rx[u], ry[u]);
-                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
+                if (!mbar_wait_t(empty0 + 8 * s, ph ^ 1u, abort_flag, my_acc)) {
                     fail(cc.cd);
                     ok = false;
                     break;
                 }
-                store_row<kFp8>(sB + s * kChunk, (uint32_t)r, w);
+                store_units<kFp8>(sB + s * kChunk, (uint32_t)r, (uint32_t)(4 * part), w0, w1);
                 fence_proxy_async();
                 mbar_arrive(fullB0 + 8 * s);
                 ++q;
                 cursor_next(cc, cds, tiles, my_tiles);
             }
         }
-    } else {
+    } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue (warps 2..9)
         const int tid = threadIdx.x - kEpiWarp0 * 32;   // 0..255
-        const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;
+        const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;  // TMEM lane quadrant
         const int L = quad * 32 + lane;                 // TMEM lane = A row = (kk, z)
         const int kk = L >> 1, z = L & 1;
         int cnt = 0, cur = -1;
@@ -489,7 +538,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             }
             const int M = cd.pl.M;
             const int i = tile.x, j0 = tile.y * kJB, k = tile.z * kKB + kk;
-            if (!mbar_wait(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag)) fail(&cd);
+            if (!mbar_wait_t(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag, my_acc)) fail(&cd);
             epi_bar();  // uniform decision: every epilogue thread stops on the same tile
             if (tid == 0) es.stop = *abort_flag;
             epi_bar();
@@ -589,6 +638,17 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         }
         if (cur >= 0) epi_prune(cds[cur], es, cnt, tid, true);
     }
+    if (prof) {
+        const unsigned long long total = (unsigned long long)(clock64() - t_start);
+        if (warp == 0 && lane == 0) atomicAdd(prof + 0, w_acc);
+        if (warp == kWarpMma && lane == 0) {
+            atomicAdd(prof + 1, w_acc);
+            atomicAdd(prof + 2, busy);
+        }
+        if (warp >= kProdWarp0 && lane == 0) atomicAdd(prof + 3, w_acc);
+        if (warp >= kEpiWarp0 && warp < kProdWarp0 && lane == 0) atomicAdd(prof + 4, w_acc);
+        if (threadIdx.x == 0) atomicAdd(prof + 5, total);
+    }
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
@@ -645,19 +705,20 @@ cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0
 }
 
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                            bool fp8, int grid, cudaStream_t st) {
+                            bool fp8, int grid, cudaStream_t st, unsigned long long* prof) {
     const size_t smem = scan_mma_smem();
     cudaError_t e;
+
     if (fp8) {
         e = cudaFuncSetAttribute(scan_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        scan_mma_kernel<true><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles);
+        scan_mma_kernel<true><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
     } else {
         e = cudaFuncSetAttribute(scan_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        scan_mma_kernel<false><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles);
+        scan_mma_kernel<false><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
     }
     return cudaGetLastError();
 }

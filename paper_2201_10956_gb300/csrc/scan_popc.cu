@@ -279,10 +279,16 @@ size_t scan_popc8_smem(const Planes& pl) {
     return (size_t)4 * (pl.W4[0] + pl.W4[1]) * sizeof(uint4);
 }
 
+// The dynamic shared-memory cap is a per-kernel attribute: set it to the largest size any
+// data set can need (not to this one's), so launches of several data sets (a batch graph)
+// all stay within it.
+constexpr int kPopcSmemCap = 200 * 1024;
+
 template <bool kEight>
 static cudaError_t occupancy(int block, size_t smem, int* ctas_per_sm) {
+    if (smem > (size_t)kPopcSmemCap) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<kEight>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPopcSmemCap);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, scan_popc_kernel<kEight>,
                                                          block, smem);

@@ -48,7 +48,10 @@ class Stats(ctypes.Structure):
                 ("select_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
                 ("pack_ms", ctypes.c_float), ("path", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("k2_rel_bound", ctypes.c_float), ("k2_abs_bound", ctypes.c_float)]
+                ("k2_rel_bound", ctypes.c_float), ("k2_abs_bound", ctypes.c_float),
+                ("wait_loader", ctypes.c_float), ("wait_mma_operands", ctypes.c_float),
+                ("wait_mma_accum", ctypes.c_float), ("wait_producers", ctypes.c_float),
+                ("wait_epilogue", ctypes.c_float)]
 
 
 _lib = None
