@@ -336,7 +336,7 @@ __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds
 }
 
 template <bool kFp8>
-__global__ void __maxnreg__(112)  // 576 threads x 112 registers: one CTA per SM
+__global__ void __launch_bounds__(kThreads, 1)  // 18 warps: 5 on one SM sub-partition -> 96 regs
 scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
                 unsigned long long* __restrict__ prof) {
     // prof (optional): per role, cycles spent waiting, summed over CTAs:
