@@ -13,9 +13,10 @@
 // (j, a, b), K = 128 samples (FP8 E4M3 operands) or 64 samples (FP16) per stage, four
 // tcgen05.mma per stage.  Both classes accumulate into separate 128-column TMEM regions;
 // two accumulator buffers (512 columns) let the epilogue of one tile overlap the MMAs of
-// the next.  A is pre-tiled in HBM in the exact 128B-swizzled shared-memory image and
-// fetched with one cp.async.bulk per stage; B is expanded from the bit planes by four
-// producer warps straight into the swizzled layout.
+// the next.  The one-hot matrix is pre-tiled in HBM in the exact 128B-swizzled shared-memory
+// image; per stage cp.async.bulk fetches the A chunk (third SNPs), the one-hot rows of the
+// second SNPs (Y) and of the first SNP (X), and four producer warps form B = Y AND X byte by
+// byte straight into the swizzled layout.
 //
 // Warp roles (18 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
 // (two warps per TMEM lane quadrant), 10..17 = B producers (two threads per B row).  Every mbarrier wait is
@@ -31,12 +32,14 @@ constexpr int kKB = 64;                  // third SNPs per tile (A rows = 2 per 
 constexpr int kJB = 32;                  // second SNPs per tile (B rows = 4 per SNP)
 constexpr int kStages = 4;
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
-// 18 warps: 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps per
-// TMEM lane quadrant), 10..17 = producers (two threads per B row).
-constexpr int kThreads = 576;
+// 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps
+// per TMEM lane quadrant), 10..13 = B producers (one thread per B row).
+constexpr int kThreads = 448;
 constexpr int kWarpMma = 1;
 constexpr int kEpiWarp0 = 2, kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
-constexpr int kProdWarp0 = 10, kProdWarps = 8, kProdThreads = kProdWarps * 32;
+constexpr int kProdWarp0 = 10, kProdWarps = 4, kProdThreads = kProdWarps * 32;
+constexpr int kYChunk = kChunk / 2;      // one-hot rows (j, b) of 32 second SNPs: 64 rows
+constexpr int kXBytes = 256;             // one-hot rows (i, 0) and (i, 1): 2 rows
 constexpr int kTmemCols = 512;
 constexpr int kPrefetch = 4;             // producer prefetch distance (stages)
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
@@ -206,20 +209,6 @@ __device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint3
     }
 }
 
-// The half of K-step ks's bits that producer part p (units 4p .. 4p+3) needs: FP8 words
-// 2p, 2p+1 of the 128-sample group; FP16 word p of the step's 64 samples.
-template <bool kFp8>
-__device__ __forceinline__ uint2 part_bits(const Planes& pl, int c, int plane, int m, int ks,
-                                           int part) {
-    if (m >= pl.M) return make_uint2(0, 0);
-    const int w4 = kFp8 ? ks : (ks >> 1);
-    const uint4* g = pl.planes + pl.coff[c] + ((size_t)plane * pl.W4[c] + w4) * pl.M + m;
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(g);
-    if (kFp8) return __ldg(reinterpret_cast<const uint2*>(w) + part);
-    return make_uint2(__ldg(w + ((ks & 1) * 2 + part)), 0);
-}
-
-// Words of K-step ks of class c, plane p, SNP m (zero words past the class or for m >= M).
 template <bool kFp8>
 __device__ __forceinline__ uint4 step_bits(const Planes& pl, int c, int p, int m, int ks) {
     if (m >= pl.M) return make_uint4(0, 0, 0, 0);
@@ -336,7 +325,7 @@ __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds
 }
 
 template <bool kFp8>
-__global__ void __launch_bounds__(kThreads, 1)  // 18 warps: 5 on one SM sub-partition -> 96 regs
+__global__ void __launch_bounds__(kThreads, 1)
 scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
                 unsigned long long* __restrict__ prof) {
     // prof (optional): per role, cycles spent waiting, summed over CTAs:
@@ -351,13 +340,15 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
     uint8_t* base = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* sA = base;
-    uint8_t* sB = base + kStages * kChunk;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * kStages * kChunk);
+    uint8_t* sA = base;                                    // [kStages][16 KB]
+    uint8_t* sB = base + kStages * kChunk;                 // [kStages][16 KB]
+    uint8_t* sY = base + 2 * kStages * kChunk;             // [kStages][8 KB]
+    uint8_t* sX = sY + kStages * kYChunk;                  // [kStages][256 B]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sX + kStages * kXBytes);
     // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], acc_empty[2], drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    EpiShared& es = *reinterpret_cast<EpiShared*>(base + 2 * kStages * kChunk + 256);
+    EpiShared& es = *reinterpret_cast<EpiShared*>(reinterpret_cast<uint8_t*>(bars) + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t fullA0 = smem_u32(bars), fullB0 = smem_u32(bars + kStages),
@@ -414,11 +405,22 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     fail(cu.cd);
                     break;
                 }
-                const long long chunk =
-                    (cu.c ? cu.cd->oh_off1 : 0) + (long long)cu.tile.z * (cu.c ? cu.ks1 : cu.ks0) + cu.ks;
-                mbar_arrive_tx(fullA0 + 8 * s, kChunk);
-                bulk_g2s(smem_u32(sA + s * kChunk), cu.cd->oh + chunk * kChunk, kChunk,
-                         fullA0 + 8 * s);
+                // A: one-hot rows (k, z) of the tile's 64 third SNPs; Y: rows (j, b) of its 32
+                // second SNPs (half of their 64-SNP chunk); X: rows (i, 0), (i, 1).  All three
+                // come from the same pre-tiled one-hot matrix of the class.
+                const long long base_c = cu.c ? cu.cd->oh_off1 : 0;
+                const int nks = cu.c ? cu.ks1 : cu.ks0;
+                const uint8_t* oh = cu.cd->oh;
+                const long long ca = base_c + (long long)cu.tile.z * nks + cu.ks;
+                const long long cy = base_c + (long long)(cu.tile.y >> 1) * nks + cu.ks;
+                const long long cx = base_c + (long long)(cu.tile.x >> 6) * nks + cu.ks;
+                const uint32_t xr = 2u * (uint32_t)(cu.tile.x & 63);
+                mbar_arrive_tx(fullA0 + 8 * s, kChunk + kYChunk + kXBytes);
+                bulk_g2s(smem_u32(sA + s * kChunk), oh + ca * kChunk, kChunk, fullA0 + 8 * s);
+                bulk_g2s(smem_u32(sY + s * kYChunk), oh + cy * kChunk + (cu.tile.y & 1) * kYChunk,
+                         kYChunk, fullA0 + 8 * s);
+                bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
+                         kXBytes, fullA0 + 8 * s);
             }
             // drain: the copies of the last stages issued must land before the CTA exits
             for (long long d = (q > kStages ? q - kStages : 0); d < q; ++d) {
@@ -472,47 +474,40 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             mbar_wait(drain0, 0, &no_abort);
         }
     } else if (warp >= kProdWarp0) {
-        // ------------------------------------------------ B producers: row r = (jj, a, b),
-        // two threads per row, each expanding four of the row's eight 16-byte units
-        const int pt = threadIdx.x - kProdWarp0 * 32;
-        const int r = pt >> 1, part = pt & 1;
+        // ------------------------------------------------ B producers: row r = (jj, a, b)
+        // B row (j, a, b) = one-hot row (j, b) AND one-hot row (i, a), byte by byte (0x38 & 0x38
+        // = 0x38 for E4M3 1.0; 0x3C00 & 0x3C00 for FP16), read from the staged Y and X rows and
+        // written in the 128B-swizzled layout.
+        const int r = threadIdx.x - kProdWarp0 * 32;
         const int jj = r >> 2, ga = (r >> 1) & 1, gb = r & 1;
-        uint2 rx[kPrefetch], ry[kPrefetch];
-        StepCursor fc{}, cc{};   // fetch cursor runs kPrefetch steps ahead of the consume cursor
-        fc.tl = 0;
+        const uint32_t yr = (uint32_t)(2 * jj + gb);
+        StepCursor cc{};
         cc.tl = 0;
-        cursor_load(fc, cds, tiles, my_tiles);
         cursor_load(cc, cds, tiles, my_tiles);
-        auto fetch = [&](uint2& x, uint2& y) {
-            if (!fc.valid) return;
-            const Planes& pl = fc.cd->pl;
-            x = part_bits<kFp8>(pl, fc.c, ga, fc.tile.x, fc.ks, part);
-            y = part_bits<kFp8>(pl, fc.c, gb, fc.tile.y * kJB + jj, fc.ks, part);
-            cursor_next(fc, cds, tiles, my_tiles);
-        };
-#pragma unroll
-        for (int u = 0; u < kPrefetch; ++u) fetch(rx[u], ry[u]);
         bool ok = true;
         long long q = 0;
-        while (cc.valid && ok) {
-#pragma unroll
-            for (int u = 0; u < kPrefetch; ++u) {
-                if (!cc.valid || !ok) break;
-                const int s = (int)(q % kStages);
-                const unsigned ph = (unsigned)((q / kStages) & 1);
-                const uint32_t w0 = rx[u].x & ry[u].x, w1 = rx[u].y & ry[u].y;
-                fetch(rx[u], ry[u]);
-                if (!mbar_wait_t(empty0 + 8 * s, ph ^ 1u, abort_flag, my_acc)) {
-                    fail(cc.cd);
-                    ok = false;
-                    break;
-                }
-                store_units<kFp8>(sB + s * kChunk, (uint32_t)r, (uint32_t)(4 * part), w0, w1);
-                fence_proxy_async();
-                mbar_arrive(fullB0 + 8 * s);
-                ++q;
-                cursor_next(cc, cds, tiles, my_tiles);
+        for (; cc.valid && ok; ++q, cursor_next(cc, cds, tiles, my_tiles)) {
+            const int s = (int)(q % kStages);
+            const unsigned ph = (unsigned)((q / kStages) & 1);
+            // full A/Y/X of step q also means the loader found stage s free, so B is free too
+            if (!mbar_wait_t(fullA0 + 8 * s, ph, abort_flag, my_acc)) {
+                fail(cc.cd);
+                ok = false;
+                break;
             }
+            const uint32_t xp = (2u * (uint32_t)(cc.tile.x & 63) + (uint32_t)ga) & 7u;
+            const uint8_t* ys = sY + s * kYChunk;
+            const uint8_t* xs = sX + s * kXBytes + ga * 128;
+            uint8_t* bs = sB + s * kChunk;
+#pragma unroll
+            for (uint32_t u = 0; u < 8; ++u) {
+                const uint4 y = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
+                const uint4 x = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
+                *reinterpret_cast<uint4*>(bs + sw128_off((uint32_t)r, u)) =
+                    make_uint4(y.x & x.x, y.y & x.y, y.z & x.z, y.w & x.w);
+            }
+            fence_proxy_async();
+            mbar_arrive(fullB0 + 8 * s);
         }
     } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue (warps 2..9)
@@ -606,13 +601,12 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                                  __ldg(pt.marg + (size_t)c * M + j), mz[c], pt.n_c[c],
                                  c ? r1 : r0);
                     }
-                    // guard the log-factorial lookups: every cell must lie in [0, N_c]
-                    bool sane = true;
+                    // guard the log-factorial lookups: derive27 makes every class sum N_c, so
+                    // no negative cell means every cell lies in [0, N_c]
+                    int neg = 0;
 #pragma unroll
-                    for (int q = 0; q < kCells; ++q)
-                        sane &= (unsigned)r0[q] <= (unsigned)pt.n_c[0] &&
-                                (unsigned)r1[q] <= (unsigned)pt.n_c[1];
-                    if (!sane) {
+                    for (int q = 0; q < kCells; ++q) neg |= r0[q] | r1[q];
+                    if (neg < 0) {
                         atomicOr(&cd.ctrl->status, kStBadCount);
                         continue;
                     }
@@ -689,7 +683,7 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
 }  // namespace
 
 size_t scan_mma_smem() {
-    return 1024 + 2 * kStages * kChunk + 256 + sizeof(EpiShared) + 64;  // bars + slot < 256 B
+    return 1024 + kStages * (2 * kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 64;
 }
 
 int mma_samples_per_step(bool fp8) { return fp8 ? 128 : 64; }
