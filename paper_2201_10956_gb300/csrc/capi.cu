@@ -39,8 +39,10 @@ int cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-// Host-side fault injection for tests of the error paths: EPI3_FAULT=alloc makes the
-// next device allocation fail, EPI3_FAULT=launch makes the next scan launch fail.
+// Fault injection for tests of the error paths, all without faulting the GPU:
+// EPI3_FAULT=alloc makes device allocations fail, EPI3_FAULT=launch makes scan launches fail,
+// EPI3_FAULT=timeout makes the tensor-core scan's MMA issuer wait on a barrier nobody
+// signals, so its bounded wait runs out (1 s) and the scan returns EPI3_ERR_TIMEOUT.
 bool inject(const char* what) {
     const char* f = getenv("EPI3_FAULT");
     return f && strcmp(f, what) == 0;
@@ -417,6 +419,7 @@ CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k)
     cd.cand_cap = h->cand_cap;
     cd.top_k = top_k;
     cd.dbg = h->dbg;
+    cd.inject_timeout = inject("timeout") ? 1 : 0;
     return cd;
 }
 
@@ -453,7 +456,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.n_rescored = h->h_ctrl->n_final;
     s.path = path;
     s.grid = grid;
-    s.block = 576;
+    s.block = 448;
     s.kernel_launches = 5;
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
     if (h->profile && h->d_prof) {
@@ -1245,7 +1248,7 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
     }
     s.path = n_mma == b->n ? EPI3_PATH_MMA : (n_mma == 0 ? EPI3_PATH_POPC8 : EPI3_PATH_AUTO);
     s.grid = b->sm_count;
-    s.block = 576;
+    s.block = 448;
     s.kernel_launches = b->n + (b->n_tiles > 0 ? 1 : 0) + (b->n - n_mma) + 3 * b->n;
     // device time of the whole graph replay (scan kernels + candidate stages + read-back);
     // the scan kernels are > 99 % of it

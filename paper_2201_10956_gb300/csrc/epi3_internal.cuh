@@ -130,6 +130,7 @@ struct CohortDev {
     long long cand_cap;
     int top_k;
     float* dbg;
+    int inject_timeout;       // test hook: the MMA issuer first waits on a barrier nobody signals
 };
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...

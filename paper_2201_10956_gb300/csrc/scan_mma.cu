@@ -434,6 +434,10 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         if (lane == 0) {
             long long q = 0;
             bool ok = true;
+            if (cds[0].inject_timeout) {  // test hook: a wait that can only run out (1 s)
+                if (!mbar_wait(drain0, 0, abort_flag)) fail(cds);
+                ok = false;
+            }
             for (long long tl = 0; tl < my_tiles && ok; ++tl) {
                 const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
                 const CohortDev* cd = cds + tile.w;

@@ -114,3 +114,19 @@ def test_tensor_scan_medium_sampled(name):
         tr, sc = h.scan(10)
     assert np.array_equal(tr, ref_t) and np.array_equal(sc, ref_s)
     assert np.array_equal(oracle.scores(g, ph, tr), sc)
+
+
+def test_bounded_wait_times_out_and_context_survives(monkeypatch):
+    # a device wait that can only run out: the kernel must report EPI3_ERR_TIMEOUT after its
+    # 1 s limit, release its resources, and leave the context usable
+    g, ph = pins.tiny_data(40, 300, 120, seed=77)
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", "mma")
+        monkeypatch.setenv("EPI3_FAULT", "timeout")
+        with pytest.raises(epi.Epi3Error) as ei:
+            h.scan(5)
+        assert ei.value.code == epi.ERR_TIMEOUT
+        monkeypatch.delenv("EPI3_FAULT")
+        tr, sc = h.scan(5)
+    otr, osc, _ = oracle.scan_topk(g, ph, 5)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
