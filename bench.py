@@ -43,9 +43,12 @@ METRIC = "tera sample-triplets/s (K2 scored)"
 UNIT = "Tsample-triplets/s"
 POPC_PER_SM_CLK = 16          # 32-bit POPC issue rate per SM per clock (measured, see DESIGN)
 L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
-# DRAM bytes per launch of the dominant kernel from one ncu capture (None until captured
-# for the current kernel), keyed by (path, workload).
-TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel from one single-pass ncu capture of the bench command, keyed by (path, workload);
+# an entry is removed whenever that kernel changes.
+TRAFFIC = {
+    ("mma", "large"): 1.86e9 + 16.73e6,    # scan_mma_kernel<e4m3>, 2048 x 16384
+}
 
 
 def env_int(name, default):

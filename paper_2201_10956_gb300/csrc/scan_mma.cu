@@ -18,8 +18,8 @@
 // second SNPs (Y) and of the first SNP (X), and four producer warps form B = Y AND X byte by
 // byte straight into the swizzled layout.
 //
-// Warp roles (18 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
-// (two warps per TMEM lane quadrant), 10..17 = B producers (two threads per B row).  Every mbarrier wait is
+// Warp roles (14 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
+// (two warps per TMEM lane quadrant), 10..13 = B producers (one thread per B row).  Every mbarrier wait is
 // bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
 // frees TMEM and returns.
 #include "epi3_internal.cuh"
