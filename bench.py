@@ -46,9 +46,7 @@ L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel from one single-pass ncu capture of the bench command, keyed by (path, workload);
 # an entry is removed whenever that kernel changes.
-TRAFFIC = {
-    ("mma", "large"): 1.86e9 + 16.73e6,    # scan_mma_kernel<e4m3>, 2048 x 16384
-}
+TRAFFIC = {}
 
 
 def env_int(name, default):

@@ -2,38 +2,42 @@
 //
 // For a fixed first SNP i and class c the 8 cells with genotypes in {0,1} of every
 // triplet (i, j, k) are one GEMM over the class's samples s:
-//     D[(k, z), (j, a, b)] = sum_s [g_k(s) = z] * ([g_i(s) = a] & [g_j(s) = b]),
-// A = one-hot rows of the third SNP (2 rows per SNP), B = one-hot pair products (4 rows
-// per second SNP), both 0/1 values, FP32 accumulation in TMEM (counts < 2^24: exact).
+//     D[(j, a, b), (k, z)] = sum_s ([g_i(s) = a] & [g_j(s) = b]) * [g_k(s) = z],
+// A = one-hot pair products (4 rows per second SNP), B = one-hot rows of the third SNP
+// (2 rows per SNP), both 0/1 values, FP32 accumulation in TMEM (counts < 2^24: exact).
 // The other 19 cells follow exactly from pair tables and marginals (derive27), then K2
 // and the candidate band exactly as in the POPC scan.  (The paper's kernels use POPCNT,
 // Sec. IV; its related work, Sec. II, points at tensor-core formulations.)
 //
-// Tile = (i, 64 third SNPs, 32 second SNPs): MMA M = 128 rows (k, z), N = 128 columns
-// (j, a, b), K = 128 samples (FP8 E4M3 operands) or 64 samples (FP16) per stage, four
-// tcgen05.mma per stage.  Both classes accumulate into separate 128-column TMEM regions;
-// two accumulator buffers (512 columns) let the epilogue of one tile overlap the MMAs of
-// the next.  The one-hot matrix is pre-tiled in HBM in the exact 128B-swizzled shared-memory
-// image; per stage cp.async.bulk fetches the A chunk (third SNPs), the one-hot rows of the
-// second SNPs (Y) and of the first SNP (X), and four producer warps form B = Y AND X byte by
-// byte straight into the swizzled layout.
+// Tile = (i, 32 second SNPs, 64 third SNPs): MMA M = 128 rows (j, a, b), N = 128 columns
+// (k, z), K = 128 samples (FP8 E4M3 operands) or 64 samples (FP16) per stage, four
+// tcgen05.mma per stage.  The one-hot matrix is pre-tiled in HBM in the exact 128B-swizzled
+// shared-memory image; per stage cp.async.bulk fetches the third-SNP chunk (the MMA's B
+// operand, read from shared memory), the one-hot rows of the second SNPs (Y) and of the
+// first SNP (X).  Four producer warps form A = Y AND X in registers and store it straight
+// into tensor memory (tcgen05.st), where the MMA reads it: the product never passes through
+// shared memory, whose bandwidth bounds this kernel.
 //
-// Warp roles (14 warps): 0 = A loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue
-// (two warps per TMEM lane quadrant), 10..13 = B producers (one thread per B row).  Every mbarrier wait is
-// bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
-// frees TMEM and returns.
+// Tensor memory (512 columns): a ring of three 128-column accumulator regions, one per
+// (tile, class) segment, so the epilogue of a tile overlaps the next tile's first class;
+// then four 32-column A stages.
+//
+// Warp roles (14 warps): 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 =
+// epilogue (two warps per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM
+// lane).  Every mbarrier wait is bounded; on timeout the kernel records kStTimeout, waits
+// for its own bulk copies, frees TMEM and returns.
 #include "epi3_internal.cuh"
 
 namespace epi3 {
 
 namespace {
 
-constexpr int kKB = 64;                  // third SNPs per tile (A rows = 2 per SNP)
-constexpr int kJB = 32;                  // second SNPs per tile (B rows = 4 per SNP)
+constexpr int kKB = 64;                  // third SNPs per tile (B rows = 2 per SNP)
+constexpr int kJB = 32;                  // second SNPs per tile (A rows = 4 per SNP)
 constexpr int kStages = 4;
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
 // 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps
-// per TMEM lane quadrant), 10..13 = B producers (one thread per B row).
+// per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM lane).
 constexpr int kThreads = 448;
 constexpr int kWarpMma = 1;
 constexpr int kEpiWarp0 = 2, kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
@@ -41,7 +45,10 @@ constexpr int kProdWarp0 = 10, kProdWarps = 4, kProdThreads = kProdWarps * 32;
 constexpr int kYChunk = kChunk / 2;      // one-hot rows (j, b) of 32 second SNPs: 64 rows
 constexpr int kXBytes = 256;             // one-hot rows (i, 0) and (i, 1): 2 rows
 constexpr int kTmemCols = 512;
-constexpr int kPrefetch = 4;             // producer prefetch distance (stages)
+constexpr int kRegions = 3;              // 128-column accumulator regions (columns 0..383)
+constexpr uint32_t kProdCol0 = 384;      // A stages: 32 columns (128 bytes of K) each
+constexpr uint32_t kProdCols = 32;
+static_assert(kRegions * 128 + kStages * kProdCols <= kTmemCols, "tensor memory budget");
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
 constexpr int kCandCapMma = 1024;
 constexpr int kRoundMax = 2 * kEpiThreads;   // appends per epilogue round at most
@@ -101,9 +108,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -114,20 +118,36 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(mbar) : "memory");
 }
+// D (+)= A * B^T with A (128 rows x 32 bytes of K) in tensor memory at column `a`.
 template <bool kFp8>
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t acc) {
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
     if (kFp8) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n"
+            ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+            ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
     }
+}
+// 32 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+          "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
+          "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]),
+          "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]),
+          "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {
@@ -329,10 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
                 unsigned long long* __restrict__ prof) {
     // prof (optional): per role, cycles spent waiting, summed over CTAs:
-    //   [0] A loader on empty stages, [1] MMA on full stages, [2] MMA on free accumulators,
-    //   [3] producers (thread 0 of each producer warp) on empty stages,
-    //   [4] epilogue (lane 0 of each epilogue warp) on full accumulators, [5] kernel cycles
-    //   of this CTA, [6] epilogue busy cycles, [7] producer busy cycles
+    //   [0] loader on empty stages, [1] MMA on full stages, [2] MMA on free accumulator
+    //   regions, [3] producers (lane 0 of each producer warp) on full stages, [4] epilogue
+    //   (lane 0 of each epilogue warp) on full accumulators, [5] kernel cycles of this CTA
     const long long t_start = clock64();
     unsigned long long w_acc = 0, busy = 0;
     unsigned long long* my_acc = prof ? &w_acc : nullptr;
@@ -340,21 +359,20 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
     uint8_t* base = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* sA = base;                                    // [kStages][16 KB]
-    uint8_t* sB = base + kStages * kChunk;                 // [kStages][16 KB]
-    uint8_t* sY = base + 2 * kStages * kChunk;             // [kStages][8 KB]
+    uint8_t* sK = base;                                    // [kStages][16 KB] third-SNP rows
+    uint8_t* sY = base + kStages * kChunk;                 // [kStages][8 KB]
     uint8_t* sX = sY + kStages * kYChunk;                  // [kStages][256 B]
     uint64_t* bars = reinterpret_cast<uint64_t*>(sX + kStages * kXBytes);
-    // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], acc_empty[2], drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 5);
+    // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], reg_free[3], drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 6);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     EpiShared& es = *reinterpret_cast<EpiShared*>(reinterpret_cast<uint8_t*>(bars) + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t fullA0 = smem_u32(bars), fullB0 = smem_u32(bars + kStages),
                    empty0 = smem_u32(bars + 2 * kStages), accF0 = smem_u32(bars + 3 * kStages),
-                   accE0 = smem_u32(bars + 3 * kStages + 2),
-                   drain0 = smem_u32(bars + 3 * kStages + 4);
+                   regE0 = smem_u32(bars + 3 * kStages + 2),
+                   drain0 = smem_u32(bars + 3 * kStages + 5);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -362,10 +380,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             mbar_init(fullB0 + 8 * s, kProdThreads);
             mbar_init(empty0 + 8 * s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(accF0 + 8 * b, 1);
-            mbar_init(accE0 + 8 * b, kEpiWarps);
-        }
+        for (int b = 0; b < 2; ++b) mbar_init(accF0 + 8 * b, 1);
+        for (int r = 0; r < kRegions; ++r) mbar_init(regE0 + 8 * r, kEpiWarps);
         mbar_init(drain0, 1);
         *abort_flag = 0;
         es.cnt = 0;
@@ -392,7 +408,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     };
 
     if (warp == 0) {
-        // ------------------------------------------------ A loader (lane 0)
+        // ------------------------------------------------ operand loader (lane 0)
         if (lane == 0) {
             StepCursor cu{};
             cu.tl = 0;
@@ -405,7 +421,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     fail(cu.cd);
                     break;
                 }
-                // A: one-hot rows (k, z) of the tile's 64 third SNPs; Y: rows (j, b) of its 32
+                // K: one-hot rows (k, z) of the tile's 64 third SNPs; Y: rows (j, b) of its 32
                 // second SNPs (half of their 64-SNP chunk); X: rows (i, 0), (i, 1).  All three
                 // come from the same pre-tiled one-hot matrix of the class.
                 const long long base_c = cu.c ? cu.cd->oh_off1 : 0;
@@ -416,7 +432,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 const long long cx = base_c + (long long)(cu.tile.x >> 6) * nks + cu.ks;
                 const uint32_t xr = 2u * (uint32_t)(cu.tile.x & 63);
                 mbar_arrive_tx(fullA0 + 8 * s, kChunk + kYChunk + kXBytes);
-                bulk_g2s(smem_u32(sA + s * kChunk), oh + ca * kChunk, kChunk, fullA0 + 8 * s);
+                bulk_g2s(smem_u32(sK + s * kChunk), oh + ca * kChunk, kChunk, fullA0 + 8 * s);
                 bulk_g2s(smem_u32(sY + s * kYChunk), oh + cy * kChunk + (cu.tile.y & 1) * kYChunk,
                          kYChunk, fullA0 + 8 * s);
                 bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
@@ -442,15 +458,18 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
                 const CohortDev* cd = cds + tile.w;
                 const int KS[2] = {cd->KS[0], cd->KS[1]};
-                const int buf = (int)(tl & 1);
-                if (!mbar_wait_t(accE0 + 8 * buf, (unsigned)(((tl >> 1) & 1) ^ 1), abort_flag,
-                                 prof ? &busy : nullptr)) {
-                    fail(cd);
-                    break;
-                }
-                tc_fence_after();
                 for (int c = 0; c < 2 && ok; ++c) {
-                    const uint32_t d = tmem + buf * 256 + c * 128;
+                    // accumulator region of segment (tile, class): a ring of kRegions
+                    const long long seg = 2 * tl + c;
+                    const int r = (int)(seg % kRegions);
+                    const unsigned use = (unsigned)((seg / kRegions) & 1);
+                    if (!mbar_wait_t(regE0 + 8 * r, use ^ 1u, abort_flag, prof ? &busy : nullptr)) {
+                        fail(cd);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)r * 128u;
                     for (int ks = 0; ks < KS[c]; ++ks, ++q) {
                         const int s = (int)(q % kStages);
                         const unsigned ph = (unsigned)((q / kStages) & 1);
@@ -461,16 +480,16 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                             break;
                         }
                         tc_fence_after();
-                        const uint64_t da = sw128_desc(smem_u32(sA + s * kChunk));
-                        const uint64_t db = sw128_desc(smem_u32(sB + s * kChunk));
+                        const uint32_t ta = tmem + kProdCol0 + (uint32_t)s * kProdCols;
+                        const uint64_t db = sw128_desc(smem_u32(sK + s * kChunk));
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
-                            tc_mma<kFp8>(d, da + 2 * kk, db + 2 * kk, kIdesc,
-                                         (ks > 0 || kk > 0) ? 1u : 0u);
+                            tc_mma_ts<kFp8>(d, ta + 8 * kk, db + 2 * kk, kIdesc,
+                                            (ks > 0 || kk > 0) ? 1u : 0u);
                         tc_commit(empty0 + 8 * s);
                     }
                 }
-                if (ok) tc_commit(accF0 + 8 * buf);
+                if (ok) tc_commit(accF0 + 8 * (int)(tl & 1));
             }
             // every MMA issued must complete before TMEM is released
             tc_commit(drain0);
@@ -478,13 +497,15 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             mbar_wait(drain0, 0, &no_abort);
         }
     } else if (warp >= kProdWarp0) {
-        // ------------------------------------------------ B producers: row r = (jj, a, b)
-        // B row (j, a, b) = one-hot row (j, b) AND one-hot row (i, a), byte by byte (0x38 & 0x38
-        // = 0x38 for E4M3 1.0; 0x3C00 & 0x3C00 for FP16), read from the staged Y and X rows and
-        // written in the 128B-swizzled layout.
-        const int r = threadIdx.x - kProdWarp0 * 32;
-        const int jj = r >> 2, ga = (r >> 1) & 1, gb = r & 1;
+        // ------------------------------------------------ producers: TMEM lane L = (jj, a, b)
+        // Product row (j, a, b) = one-hot row (j, b) AND one-hot row (i, a), byte by byte (0x38
+        // & 0x38 = 0x38 for E4M3 1.0; 0x3C00 & 0x3C00 for FP16), read from the staged Y and X
+        // rows (swizzled) and stored in natural K order into this stage's TMEM columns, where
+        // the MMA reads it as its A operand.
+        const int L = 32 * (warp & 3) + lane;
+        const int jj = L >> 2, ga = (L >> 1) & 1, gb = L & 1;
         const uint32_t yr = (uint32_t)(2 * jj + gb);
+        const uint32_t tl_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kProdCol0;
         StepCursor cc{};
         cc.tl = 0;
         cursor_load(cc, cds, tiles, my_tiles);
@@ -493,32 +514,45 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         for (; cc.valid && ok; ++q, cursor_next(cc, cds, tiles, my_tiles)) {
             const int s = (int)(q % kStages);
             const unsigned ph = (unsigned)((q / kStages) & 1);
-            // full A/Y/X of step q also means the loader found stage s free, so B is free too
-            if (!mbar_wait_t(fullA0 + 8 * s, ph, abort_flag, my_acc)) {
+            // the MMAs of step q - kStages have read this stage's TMEM columns; the loader's
+            // copies of step q have landed
+            const bool got = mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag) &&
+                             mbar_wait_t(fullA0 + 8 * s, ph, abort_flag, my_acc);
+            // tcgen05.st is warp-collective: the whole warp goes on or stops together
+            if (!__all_sync(0xffffffffu, got)) {
                 fail(cc.cd);
                 ok = false;
                 break;
             }
+            tc_fence_after();
             const uint32_t xp = (2u * (uint32_t)(cc.tile.x & 63) + (uint32_t)ga) & 7u;
             const uint8_t* ys = sY + s * kYChunk;
             const uint8_t* xs = sX + s * kXBytes + ga * 128;
-            uint8_t* bs = sB + s * kChunk;
+            uint32_t v[32];
 #pragma unroll
             for (uint32_t u = 0; u < 8; ++u) {
                 const uint4 y = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
                 const uint4 x = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
-                *reinterpret_cast<uint4*>(bs + sw128_off((uint32_t)r, u)) =
-                    make_uint4(y.x & x.x, y.y & x.y, y.z & x.z, y.w & x.w);
+                v[4 * u + 0] = y.x & x.x;
+                v[4 * u + 1] = y.y & x.y;
+                v[4 * u + 2] = y.z & x.z;
+                v[4 * u + 3] = y.w & x.w;
             }
-            fence_proxy_async();
+            tc_st32(tl_base + (uint32_t)s * kProdCols, v);
+            tc_wait_st();
+            tc_fence_before();
             mbar_arrive(fullB0 + 8 * s);
         }
     } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue (warps 2..9)
+        // TMEM lane L = (jj, a, b) holds, per class, the counts of (i = a, j = b, k = z) for
+        // every column 2 kk + z.  The four lanes of one jj exchange values so that each ends
+        // with all 8 cells of two (jj, kk) per 16-column group.
         const int tid = threadIdx.x - kEpiWarp0 * 32;   // 0..255
         const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;  // TMEM lane quadrant
-        const int L = quad * 32 + lane;                 // TMEM lane = A row = (kk, z)
-        const int kk = L >> 1, z = L & 1;
+        const int jj = 8 * quad + (lane >> 2), me = lane & 3;
+        const int h1 = me >> 1, l0 = me & 1;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         int cnt = 0, cur = -1;
         bool ok = true;
         for (long long tl = 0; tl < my_tiles && ok; ++tl) {
@@ -536,7 +570,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 cur = tile.w;
             }
             const int M = cd.pl.M;
-            const int i = tile.x, j0 = tile.y * kJB, k = tile.z * kKB + kk;
+            const int i = tile.x, j = tile.y * kJB + jj, kb0 = tile.z * kKB;
             if (!mbar_wait_t(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag, my_acc)) fail(&cd);
             epi_bar();  // uniform decision: every epilogue thread stops on the same tile
             if (tid == 0) es.stop = *abort_flag;
@@ -548,63 +582,78 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             tc_fence_after();
             const int KS0 = cd.KS[0], KS1 = cd.KS[1];
             const PairTables pt = cd.pt;
-            const bool krow = (k < M) && (k > i);
-            int4 pxz[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
-            int2 mz[2] = {make_int2(0, 0), make_int2(0, 0)}, mx[2];
-            if (krow) {
-                pxz[0] = __ldg(pt.pt + pair_index(i, k));
-                pxz[1] = __ldg(pt.pt + pt.n_pairs + pair_index(i, k));
-                mz[0] = __ldg(pt.marg + k);
-                mz[1] = __ldg(pt.marg + M + k);
+            long long pij = -1;
+            if (j < M && j > i) {
+                pij = pair_index(i, j);
+                if (pij < cd.pair_begin || pij >= cd.pair_end) pij = -1;
+            }
+            const bool jrow = pij >= 0;
+            int4 pxy[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+            int2 my[2] = {make_int2(0, 0), make_int2(0, 0)}, mx[2];
+            if (jrow) {
+                pxy[0] = __ldg(pt.pt + pij);
+                pxy[1] = __ldg(pt.pt + pt.n_pairs + pij);
+                my[0] = __ldg(pt.marg + j);
+                my[1] = __ldg(pt.marg + M + j);
             }
             mx[0] = __ldg(pt.marg + i);
             mx[1] = __ldg(pt.marg + M + i);
+            const uint32_t rc[2] = {(uint32_t)((2 * tl) % kRegions) * 128u,
+                                    (uint32_t)((2 * tl + 1) % kRegions) * 128u};
             for (int gi = 0; gi < 4; ++gi) {
-                const int g = half + 2 * gi;            // 16-column group = 4 second SNPs
+                const int g = half + 2 * gi;            // 16-column group = 8 third SNPs
                 uint32_t v[2][16];
-                const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
-                    tc_ld16(tmem + lane_base + buf * 256 + c * 128 + 16 * g, v[c]);
+                for (int c = 0; c < 2; ++c) tc_ld16(tmem + lane_base + rc[c] + 16 * g, v[c]);
                 tc_wait_ld();
-                int cv[2][16];
+                // n8[c][m][4a + 2b + z] for this lane's third SNPs kk = 8 g + 2 me + m
+                int n8[2][2][8];
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    cv[0][t] = KS0 ? __float2int_rn(__uint_as_float(v[0][t])) : 0;
-                    cv[1][t] = KS1 ? __float2int_rn(__uint_as_float(v[1][t])) : 0;
+                for (int c = 0; c < 2; ++c) {
+                    const bool has = c ? KS1 > 0 : KS0 > 0;
+                    int x[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) x[t] = has ? __float2int_rn(__uint_as_float(v[c][t])) : 0;
+                    // x[4 blk + e]: column 16 g + 4 blk + e; lane `me` needs block `me` of all
+                    // four lanes.  Butterfly over lane bit 1, then bit 0.
+                    int ys[2][4], yp[2][4];
+#pragma unroll
+                    for (int b0 = 0; b0 < 2; ++b0)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int lo = x[4 * b0 + e], hi = x[4 * (2 + b0) + e];
+                            ys[b0][e] = h1 ? hi : lo;
+                            yp[b0][e] = __shfl_xor_sync(0xffffffffu, h1 ? lo : hi, 2);
+                        }
+                    int w[4][4];  // w[d][e]: block `me` of lane me ^ d
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        w[0][e] = l0 ? ys[1][e] : ys[0][e];
+                        w[2][e] = l0 ? yp[1][e] : yp[0][e];
+                        w[1][e] = __shfl_xor_sync(0xffffffffu, l0 ? ys[0][e] : ys[1][e], 1);
+                        w[3][e] = __shfl_xor_sync(0xffffffffu, l0 ? yp[0][e] : yp[1][e], 1);
+                    }
+                    // lane me ^ d holds cells (a, b) = me ^ d; place by (a, b)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int t0 = l0 ? w[p ^ 1][e] : w[p][e];
+                            const int t1 = l0 ? w[p ^ 3][e] : w[p ^ 2][e];
+                            n8[c][e >> 1][2 * p + (e & 1)] = h1 ? t1 : t0;
+                        }
                 }
-                // my triplets: jj = 4g + z + 2m; the partner lane (other z) holds the
-                // other third-SNP genotype of the same (k, jj): swap what each one needs.
-                int got[2][8];
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int m = 0; m < 2; ++m)
-#pragma unroll
-                        for (int ab = 0; ab < 4; ++ab)
-                            got[c][4 * m + ab] = __shfl_xor_sync(
-                                0xffffffffu, cv[c][((1 - z) + 2 * m) * 4 + ab], 1);
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
-                    const int jj = 4 * g + z + 2 * m;
-                    const int j = j0 + jj;
-                    if (!(krow && j > i && j < k)) continue;
-                    const long long pij = pair_index(i, j);
-                    if (pij < cd.pair_begin || pij >= cd.pair_end) continue;
+                    const int k = kb0 + 8 * g + 2 * me + m;
+                    if (!(jrow && k > j && k < M)) continue;
+                    const long long pik = pair_index(i, k), pjk = pair_index(j, k);
                     int r0[kCells], r1[kCells];
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        int n8[8];
-#pragma unroll
-                        for (int ab = 0; ab < 4; ++ab) {
-                            n8[2 * ab + z] = cv[c][(z + 2 * m) * 4 + ab];  // n8[4a + 2b + gz]
-                            n8[2 * ab + (1 - z)] = got[c][4 * m + ab];
-                        }
-                        derive27(n8, __ldg(pt.pt + c * pt.n_pairs + pij), pxz[c],
-                                 __ldg(pt.pt + c * pt.n_pairs + pair_index(j, k)), mx[c],
-                                 __ldg(pt.marg + (size_t)c * M + j), mz[c], pt.n_c[c],
-                                 c ? r1 : r0);
-                    }
+                    for (int c = 0; c < 2; ++c)
+                        derive27(n8[c][m], pxy[c], __ldg(pt.pt + c * pt.n_pairs + pik),
+                                 __ldg(pt.pt + c * pt.n_pairs + pjk), mx[c], my[c],
+                                 __ldg(pt.marg + (size_t)c * M + k), pt.n_c[c], c ? r1 : r0);
                     // guard the log-factorial lookups: derive27 makes every class sum N_c, so
                     // no negative cell means every cell lies in [0, N_c]
                     int neg = 0;
@@ -632,7 +681,10 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(accE0 + 8 * buf);
+            if (lane == 0) {
+                mbar_arrive(regE0 + 8 * (int)((2 * tl) % kRegions));
+                mbar_arrive(regE0 + 8 * (int)((2 * tl + 1) % kRegions));
+            }
         }
         if (cur >= 0) epi_prune(cds[cur], es, cnt, tid, true);
     }
@@ -687,7 +739,7 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
 }  // namespace
 
 size_t scan_mma_smem() {
-    return 1024 + kStages * (2 * kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 64;
+    return 1024 + kStages * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 64;
 }
 
 int mma_samples_per_step(bool fp8) { return fp8 ? 128 : 64; }
