@@ -139,10 +139,11 @@ def shard_pairs(m, world, rank):
     return pair_at(lo_t), pair_at(hi_t)
 
 
-PATH_NAMES = {1: "popc", 2: "popc8", 3: "mma", 4: "mma16"}
+PATH_NAMES = {1: "popc", 2: "popc8", 3: "mma", 4: "mma16", 5: "mma4"}
 DTYPES = {1: "u32 popc / int32 counts", 2: "u32 popc / int32 counts",
           3: "e4m3 0/1 x e4m3 0/1 -> fp32 (exact integer counts)",
-          4: "f16 0/1 x f16 0/1 -> fp32 (exact integer counts)"}
+          4: "f16 0/1 x f16 0/1 -> fp32 (exact integer counts)",
+          5: "e2m1 0/1 x e2m1 0/1, ue8m0 block scales 1.0 -> fp32 (exact integer counts)"}
 
 
 def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config):
@@ -151,20 +152,22 @@ def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config):
     POPC forms: 27 (paper's form) or 8 (8-cell form) 32-bit POPC per 32-sample word and
     class, i.e. cells/32 POPC per sample-triplet; peak = SMs x max SM clock x 16 POPC/SM/clk.
     Tensor forms: 8 useful MACs = 16 FLOP per sample-triplet; peak = the measured dense bf16
-    rate (fp16 runs at the bf16 rate; e4m3 at 2x, the nominal fp8/bf16 ratio).
+    rate times the nominal dense ratio of the operand type to bf16 (fp16 1x, e4m3 2x,
+    e2m1 6x: 2.25 / 4.5 / 13.5 PFLOP/s nominal).
     """
     units = gen.n_triplets(m) * n / world          # sample-triplets per launch
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     traffic = TRAFFIC.get((PATH_NAMES.get(path), config))
-    if path in (3, 4):
+    if path in (3, 4, 5):
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak = bf16 * (2.0 if path == 3 else 1.0)
+        ratio, elem = {3: (2.0, "e4m3"), 4: (1.0, "f16"), 5: (6.0, "e2m1")}[path]
+        peak = bf16 * ratio
         achieved = units * 16.0 / kern_s / 1e12
-        return {"bound": "tensor", "kernel": f"scan_mma_kernel<{'e4m3' if path == 3 else 'f16'}>",
+        return {"bound": "tensor", "kernel": f"scan_mma_kernel<{elem}>",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst)"
-                             + (" x 2 (e4m3/bf16 nominal ratio)" if path == 3 else ""),
+                             + (f" x {ratio:g} ({elem}/bf16 nominal ratio)" if ratio != 1.0 else ""),
                 "work_note": "16 FLOP (8 useful 0/1 MACs) per sample-triplet; tile waste excluded"}
     cells = 8.0 if path == 2 else 27.0
     achieved = units * cells / 32.0 / kern_s
@@ -290,17 +293,18 @@ def run_batch(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(local_rank)
     peaks = read_peaks()
     kern_s = statistics.mean(kern_ms) / 1000.0
-    mma_units = sum(gen.n_triplets(d.n_snps) * d.n_samples for d, p in zip(cohorts, paths) if p == 3)
+    mma_units = sum(gen.n_triplets(d.n_snps) * d.n_samples for d, p in zip(cohorts, paths) if p == 5)
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     achieved = mma_units * 16.0 / kern_s / 1e12
-    roofline = {"bound": "tensor", "kernel": "scan_mma_kernel<e4m3> (one persistent launch, all "
+    roofline = {"bound": "tensor", "kernel": "scan_mma_kernel<e2m1> (one persistent launch, all "
                 "tensor-path cohorts) + scan_popc_kernel<8-cell> launches",
-                "achieved": achieved, "peak": 2 * bf16, "unit": "TFLOP/s",
-                "frac": achieved / (2 * bf16), "traffic": None,
-                "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst) x 2 (e4m3/bf16)",
+                "achieved": achieved, "peak": 6 * bf16, "unit": "TFLOP/s",
+                "frac": achieved / (6 * bf16), "traffic": None,
+                "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst) x 6 (e2m1/bf16 "
+                             "nominal ratio)",
                 "work_note": "16 FLOP per sample-triplet of the tensor-path cohorts over the "
                              "whole scan phase (POPC cohorts' time included)",
-                "kernel_ms": 1000 * kern_s, "tensor_cohorts": int((paths == 3).sum()),
+                "kernel_ms": 1000 * kern_s, "tensor_cohorts": int((paths == 5).sum()),
                 "popc8_cohorts": int((paths == 2).sum())}
     e2e = None
     if not args.no_e2e and world == 1:
@@ -319,7 +323,7 @@ def run_batch(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak" if world > 1 else "strong",
-            "vs_baseline": None, "dtype": DTYPES[3], "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPES[5], "data": "synthetic",
             "config": {"workload": f"batch: {WORKLOADS['batch']}", "path": "tuned per cohort",
                        "top_k": k, "l2": "flushed before every timed step (512 MB write)",
                        "wall_s": wall, "sample_triplets": units},

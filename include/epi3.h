@@ -51,9 +51,11 @@ extern "C" {
 #define EPI3_PATH_POPC8 2 /* 8 cells (genotypes 0/1) by AND + POPC, 19 derived exactly from
                              pair tables and marginals */
 #define EPI3_PATH_MMA 3   /* tensor cores: the 8 cells as a GEMM of one-hot 0/1 E4M3 operands
-                             (tcgen05 kind::f8f6f4, FP32 accumulation), 19 derived; the default
-                             (auto) scan path up to about 8700 SNPs, POPC8 beyond */
+                             (tcgen05 kind::f8f6f4, FP32 accumulation), 19 derived */
 #define EPI3_PATH_MMA16 4 /* the same GEMM with FP16 operands (tcgen05 kind::f16) */
+#define EPI3_PATH_MMA4 5  /* the same GEMM with FP4 E2M1 operands, two per byte, every 32-element
+                             block scaled by 2^0 (tcgen05 kind::mxf4, FP32 accumulation); the
+                             default (auto) scan path up to about 8700 SNPs, POPC8 beyond */
 
 #define EPI3_MAX_TOPK 512
 
@@ -213,7 +215,7 @@ int epi3_scan_noalloc(const uint8_t* genotypes, const uint8_t* phenotype, int32_
  * cohort is packed like epi3_create; a tuner times the tensor-core and 8-cell POPC scan
  * kernels on each cohort's heaviest pair slice and keeps the faster (per M/64, N/1024
  * bucket; persisted in the file named by EPI3_TUNE_CACHE; EPI3_BATCH_PATH=mma|popc8
- * forces one).  The tensor-core cohorts share ONE persistent tcgen05 launch over all their
+ * forces one, "mma" being the E2M1 tensor-core form of EPI3_PATH_MMA4).  The tensor-core cohorts share ONE persistent tcgen05 launch over all their
  * tiles; the whole scan + candidate stages + read-back is captured once in a CUDA graph and
  * replayed by every epi3_batch_scan.  The answer of each cohort is the one epi3_scan gives.
  *
@@ -238,7 +240,7 @@ int epi3_batch_destroy(epi3_batch* b);
 /* Figures of the last epi3_batch_scan: scan_kernel_ms = total_ms = device time of the graph
  * replay; pack_ms holds the tuner's time at create. */
 int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out);
-/* The path (EPI3_PATH_MMA or EPI3_PATH_POPC8) the tuner chose for each cohort. */
+/* The path (EPI3_PATH_MMA4 or EPI3_PATH_POPC8) the tuner chose for each cohort. */
 int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths);
 /* One-shot: epi3_batch_create + epi3_batch_scan + epi3_batch_destroy. */
 int epi3_scan_batch(int32_t n_cohorts, const epi3_cohort* cohorts, int32_t top_k,

@@ -92,7 +92,7 @@ struct epi3_handle {
     int2* d_marg = nullptr;
     PairTables ptab{};
     uint8_t* d_oh = nullptr;      // pre-tiled one-hot operand of the tensor-core form
-    int oh_fp8 = -1;              // element type d_oh was built for (-1: none)
+    int oh_kind = -1;             // element kind d_oh was built for (kKind*, -1: none)
     int oh_ks[2] = {0, 0};
     long long oh_off1 = 0;
     float* dbg = nullptr;         // device buffer of epi3_scan_scores (during that call only)
@@ -279,11 +279,11 @@ int ensure_pair_tables(epi3_handle* h) {
 }
 
 // Tensor-core form: pre-tiled one-hot operand (built once per element type).
-int ensure_onehot(epi3_handle* h, bool fp8) {
-    if (h->d_oh && h->oh_fp8 == (fp8 ? 1 : 0)) return EPI3_OK;
+int ensure_onehot(epi3_handle* h, int kind) {
+    if (h->d_oh && h->oh_kind == kind) return EPI3_OK;
     cudaFree(h->d_oh);
     h->d_oh = nullptr;
-    const int spk = mma_samples_per_step(fp8);
+    const int spk = mma_samples_per_step(kind);
     const int ks0 = (h->N0 + spk - 1) / spk, ks1 = (h->N1 + spk - 1) / spk;
     const int kbc = (h->M + 63) / 64;
     const size_t bytes = (size_t)kbc * (ks0 + ks1) * 16384;
@@ -291,9 +291,9 @@ int ensure_onehot(epi3_handle* h, bool fp8) {
     h->oh_ks[0] = ks0;
     h->oh_ks[1] = ks1;
     h->oh_off1 = (long long)kbc * ks0;
-    CK(launch_onehot(h->pl, h->d_oh, h->oh_off1, ks0, ks1, kbc, fp8, h->stream), "one-hot launch");
+    CK(launch_onehot(h->pl, h->d_oh, h->oh_off1, ks0, ks1, kbc, kind, h->stream), "one-hot launch");
     CK(cudaStreamSynchronize(h->stream), "one-hot");
-    h->oh_fp8 = fp8 ? 1 : 0;
+    h->oh_kind = kind;
     return EPI3_OK;
 }
 
@@ -338,11 +338,11 @@ int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
 long long mma_tile_estimate(long long M) { return M * M * M / 12288 + 1; }
 constexpr long long kMaxMmaTiles = 1LL << 26;
 
-// auto: the tensor-core form (E4M3 operands) when its tile list is small enough, else the
-// 8-cell POPC form.
+// auto: the tensor-core form (block-scaled E2M1 operands, the fastest measured) when its
+// tile list is small enough, else the 8-cell POPC form.
 int resolve_path(const epi3_handle* h) {
     if (h->path != EPI3_PATH_AUTO) return h->path;
-    return mma_tile_estimate(h->M) <= kMaxMmaTiles ? EPI3_PATH_MMA : EPI3_PATH_POPC8;
+    return mma_tile_estimate(h->M) <= kMaxMmaTiles ? EPI3_PATH_MMA4 : EPI3_PATH_POPC8;
 }
 
 // Candidate stage + result read-back shared by both scan forms.  Returns 1 to retry with a
@@ -423,9 +423,17 @@ CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k)
     return cd;
 }
 
+// Operand element kind of a tensor-core path.
+int kind_of_path(int path) {
+    return path == EPI3_PATH_MMA4 ? kKindE2M1 : (path == EPI3_PATH_MMA ? kKindE4M3 : kKindF16);
+}
+bool is_mma_path(int path) {
+    return path == EPI3_PATH_MMA || path == EPI3_PATH_MMA16 || path == EPI3_PATH_MMA4;
+}
+
 int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long long nt, int top_k,
                   int32_t* out_trip, double* out_scores, int32_t* n_out) {
-    const bool fp8 = path == EPI3_PATH_MMA;
+    const int kind = kind_of_path(path);
     if (!h->d_cd) CK(dev_alloc((void**)&h->d_cd, sizeof(CohortDev)), "alloc descriptor");
     const int grid = h->sm_count;
     for (int attempt = 0;; ++attempt) {
@@ -440,7 +448,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
             if (!h->d_prof) CK(dev_alloc((void**)&h->d_prof, 8 * sizeof(unsigned long long)), "alloc profile");
             CK(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), h->stream), "clear profile");
         }
-        CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, fp8, grid, h->stream,
+        CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, kind, grid, h->stream,
                            h->profile ? h->d_prof : nullptr), "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
@@ -496,15 +504,14 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     if (n_out) *n_out = 0;
     if (top_k == 0) return EPI3_OK;
     const int path = resolve_path(h);
-    if (path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8 && path != EPI3_PATH_MMA &&
-        path != EPI3_PATH_MMA16)
+    if (path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8 && !is_mma_path(path))
         return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
-    const bool mma = path == EPI3_PATH_MMA || path == EPI3_PATH_MMA16;
+    const bool mma = is_mma_path(path);
     if (mma && mma_tile_estimate(h->M) > kMaxMmaTiles)
         return fail(EPI3_ERR_UNSUPPORTED, "n_snps %d too large for the tensor-core tile list", h->M);
     if (path != EPI3_PATH_POPC) {
         int rc = ensure_pair_tables(h);
-        if (rc == EPI3_OK && mma) rc = ensure_onehot(h, path == EPI3_PATH_MMA);
+        if (rc == EPI3_OK && mma) rc = ensure_onehot(h, kind_of_path(path));
         if (rc == EPI3_OK && mma) rc = ensure_tiles(h, pb, pe);
         if (rc != EPI3_OK) return rc;
     }
@@ -790,6 +797,7 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
         else if (!strcmp(value, "popc8")) h->path = EPI3_PATH_POPC8;
         else if (!strcmp(value, "mma")) h->path = EPI3_PATH_MMA;
         else if (!strcmp(value, "mma16")) h->path = EPI3_PATH_MMA16;
+        else if (!strcmp(value, "mma4")) h->path = EPI3_PATH_MMA4;
         else return fail(EPI3_ERR_UNSUPPORTED, "path '%s' not available", value);
         return EPI3_OK;
     }
@@ -848,7 +856,7 @@ struct epi3_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<epi3_handle*> h;
-    std::vector<int> path;              // EPI3_PATH_MMA or EPI3_PATH_POPC8 per cohort
+    std::vector<int> path;              // EPI3_PATH_MMA4 or EPI3_PATH_POPC8 per cohort
     Ctrl* d_ctrls = nullptr;            // one control block per cohort, contiguous
     Ctrl* h_ctrls = nullptr;            // pinned
     CohortDev* d_cds = nullptr;
@@ -940,21 +948,22 @@ void tune_store(const TuneEntry& e) {
 
 int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
     const char* force = getenv("EPI3_BATCH_PATH");
-    if (force && !strcmp(force, "mma")) { *path_out = EPI3_PATH_MMA; return EPI3_OK; }
+    if (force && !strcmp(force, "mma")) { *path_out = EPI3_PATH_MMA4; return EPI3_OK; }
     if (force && !strcmp(force, "popc8")) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
     if (mma_tile_estimate(h->M) > kMaxMmaTiles) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
     tune_load();
     const std::string dev = device_name(b->device);
     const int mb = h->M / 64, nb = h->N / 1024;
     for (const TuneEntry& e : g_tune)
-        if (e.dev == dev && e.sms == b->sm_count && e.mb == mb && e.nb == nb) {
+        if (e.dev == dev && e.sms == b->sm_count && e.mb == mb && e.nb == nb &&
+            (e.path == EPI3_PATH_MMA4 || e.path == EPI3_PATH_POPC8)) {
             *path_out = e.path;
             return EPI3_OK;
         }
     const long long np = pairs(h->M - 1);
     const long long pe = std::max(1LL, np / 16);
     float t[2] = {0.f, 0.f};
-    const int paths[2] = {EPI3_PATH_POPC8, EPI3_PATH_MMA};
+    const int paths[2] = {EPI3_PATH_POPC8, EPI3_PATH_MMA4};
     int32_t trip[3];
     double sc;
     int32_t nout = 0;
@@ -967,7 +976,7 @@ int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
         *ms += h->stats.total_ms * 2;
     }
     h->path = EPI3_PATH_AUTO;
-    *path_out = t[1] <= t[0] ? EPI3_PATH_MMA : EPI3_PATH_POPC8;
+    *path_out = t[1] <= t[0] ? EPI3_PATH_MMA4 : EPI3_PATH_POPC8;
     tune_store(TuneEntry{dev, b->sm_count, mb, nb, *path_out});
     return EPI3_OK;
 }
@@ -1019,7 +1028,7 @@ int batch_capture(epi3_batch* b, int top_k) {
     }
     cur = "tensor scan";
     cur_c = -1;
-    if (b->n_tiles > 0) ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, true, b->sm_count, b->stream));
+    if (b->n_tiles > 0) ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, kKindE2M1, b->sm_count, b->stream));
     cur = "popc8 scan";
     for (int c = 0; c < b->n; ++c) {
         if (b->path[c] != EPI3_PATH_POPC8) continue;
@@ -1147,8 +1156,8 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
     for (int c = 0; c < n_cohorts; ++c) {
         epi3_handle* h = b->h[c];
         if ((rc = tune_path(b, h, &b->path[c], &b->tune_ms)) != EPI3_OK) return bail(rc);
-        if (b->path[c] == EPI3_PATH_MMA) {
-            if ((rc = ensure_onehot(h, true)) != EPI3_OK) return bail(rc);
+        if (b->path[c] == EPI3_PATH_MMA4) {
+            if ((rc = ensure_onehot(h, kKindE2M1)) != EPI3_OK) return bail(rc);
             append_tiles(h->M, 0, pairs(h->M - 1), c, tiles);
         }
         h->path = b->path[c];
@@ -1244,9 +1253,9 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
         s.n_triplets += m * (m - 1) * (m - 2) / 6;
         s.n_candidates += b->h_ctrls[c].n_cand;
         s.n_rescored += b->h_ctrls[c].n_final;
-        n_mma += b->path[c] == EPI3_PATH_MMA;
+        n_mma += b->path[c] == EPI3_PATH_MMA4;
     }
-    s.path = n_mma == b->n ? EPI3_PATH_MMA : (n_mma == 0 ? EPI3_PATH_POPC8 : EPI3_PATH_AUTO);
+    s.path = n_mma == b->n ? EPI3_PATH_MMA4 : (n_mma == 0 ? EPI3_PATH_POPC8 : EPI3_PATH_AUTO);
     s.grid = b->sm_count;
     s.block = 448;
     s.kernel_launches = b->n + (b->n_tiles > 0 ? 1 : 0) + (b->n - n_mma) + 3 * b->n;

@@ -112,9 +112,12 @@ cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long
 cudaError_t launch_scan_popc8(const ScanArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 size_t scan_popc8_smem(const Planes& pl);
 size_t scan_mma_smem();
-int mma_samples_per_step(bool fp8);
+// Element kinds of the tensor-core scan's 0/1 operands: FP16, FP8 E4M3, block-scaled FP4 E2M1
+// (two per byte).  A 128-byte operand row holds 64, 128 or 256 samples.
+enum { kKindF16 = 0, kKindE4M3 = 1, kKindE2M1 = 2 };
+int mma_samples_per_step(int kind);
 cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
-                          int kb_count, bool fp8, cudaStream_t st);
+                          int kb_count, int kind, cudaStream_t st);
 // One data set ("cohort") as the tensor-core scan sees it.  The kernel reads these from
 // device memory, one per tile (tile.w = cohort index), so one launch can scan many.
 struct CohortDev {
@@ -135,7 +138,7 @@ struct CohortDev {
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                            bool fp8, int grid, cudaStream_t st, unsigned long long* prof = nullptr);
+                            int kind, int grid, cudaStream_t st, unsigned long long* prof = nullptr);
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 
 // Message returned by epi3_last_error() on this thread.

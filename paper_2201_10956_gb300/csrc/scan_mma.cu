@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kKB = 64;                  // third SNPs per tile (B rows = 2 per SNP)
 constexpr int kJB = 32;                  // second SNPs per tile (A rows = 4 per SNP)
-constexpr int kStages = 4;
+constexpr int kSmStages = 6;             // shared-memory ring: K, Y, X chunks of one step
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
 // 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps
 // per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM lane).
@@ -48,7 +48,13 @@ constexpr int kTmemCols = 512;
 constexpr int kRegions = 3;              // 128-column accumulator regions (columns 0..383)
 constexpr uint32_t kProdCol0 = 384;      // A stages: 32 columns (128 bytes of K) each
 constexpr uint32_t kProdCols = 32;
-static_assert(kRegions * 128 + kStages * kProdCols <= kTmemCols, "tensor memory budget");
+constexpr uint32_t kSfCol = 480;         // E2M1 block scales: A at 480..495, B at 496..511
+constexpr int kTmStagesMax = 4;
+// tensor-memory ring of A stages: four, or three beside the block-scale columns
+template <int kKind>
+__host__ __device__ constexpr int tm_stages() { return kKind == kKindE2M1 ? 3 : 4; }
+static_assert(kRegions * 128 + 4 * kProdCols <= kTmemCols, "tensor memory budget");
+static_assert(kRegions * 128 + 3 * kProdCols <= kSfCol, "tensor memory budget (E2M1)");
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
 constexpr int kCandCapMma = 1024;
 constexpr int kRoundMax = 2 * kEpiThreads;   // appends per epilogue round at most
@@ -118,20 +124,27 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(mbar) : "memory");
 }
-// D (+)= A * B^T with A (128 rows x 32 bytes of K) in tensor memory at column `a`.
-template <bool kFp8>
+// D (+)= A * B^T with A (128 rows x 32 bytes of K) in tensor memory at column `a`; the E2M1
+// form scales every 32-element block by the UE8M0 factors at `sfa` / `sfb` (all 1.0 here).
+template <int kKind>
 __device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t acc) {
-    if (kFp8) {
+                                          uint32_t acc, uint32_t sfa, uint32_t sfb) {
+    if (kKind == kKindE4M3) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n"
             ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
-    } else {
+    } else if (kKind == kKindF16) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
             ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3,"
+            " [%5], [%6], p;\n}\n"
+            ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc), "r"(sfa), "r"(sfb) : "memory");
     }
 }
 // 32 consecutive 32-bit columns of this thread's TMEM lane.
@@ -176,6 +189,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 // Instruction descriptor: FP32 accumulator, A/B E4M3 (kind::f8f6f4) or F16 (kind::f16),
 // both K-major, N = 128, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// Block-scaled form (kind::mxf4): A/B E2M1 (format 1), UE8M0 scales (bit 23), K-major,
+// N = 128, M = 128, scale-factor data ids 0.
+constexpr uint32_t kIdescMx = (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | (1u << 23) |
+                              ((128u >> 4) << 24);
+template <int kKind>
+__host__ __device__ constexpr uint32_t idesc_of() { return kKind == kKindE2M1 ? kIdescMx : kIdesc; }
 
 // Byte offset of 16-byte unit u of row r in a 128-row, 128 B-per-row 128B-swizzled tile.
 __host__ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t u) {
@@ -190,52 +209,79 @@ __device__ __forceinline__ uint32_t nib_to_bytes(uint32_t nib, uint32_t one) {
 __device__ __forceinline__ uint32_t bits2_to_h2(uint32_t b2) {
     return ((b2 * 0x8001u) & 0x10001u) * 0x3C00u;
 }
-
-// Expand units ub .. ub+3 (16-byte units of the 128-byte row r) from their sample bits into
-// the swizzled tile.  FP8: a unit is 16 samples, the four units are the 64 bits w0 | w1 << 32;
-// FP16: a unit is 8 samples, the four units are the 32 bits of w0.
-template <bool kFp8>
-__device__ __forceinline__ void store_units(uint8_t* tile, uint32_t r, uint32_t ub, uint32_t w0,
-                                            uint32_t w1) {
-#pragma unroll
-    for (uint32_t q = 0; q < 4; ++q) {
-        uint4 v;
-        if (kFp8) {
-            const uint32_t h = ((q < 2 ? w0 : w1) >> ((q & 1) * 16)) & 0xFFFFu;
-            v.x = nib_to_bytes(h & 0xF, 0x38u);
-            v.y = nib_to_bytes((h >> 4) & 0xF, 0x38u);
-            v.z = nib_to_bytes((h >> 8) & 0xF, 0x38u);
-            v.w = nib_to_bytes(h >> 12, 0x38u);
-        } else {
-            const uint32_t b = (w0 >> (q * 8)) & 0xFFu;
-            v.x = bits2_to_h2(b & 3);
-            v.y = bits2_to_h2((b >> 2) & 3);
-            v.z = bits2_to_h2((b >> 4) & 3);
-            v.w = bits2_to_h2(b >> 6);
-        }
-        *reinterpret_cast<uint4*>(tile + sw128_off(r, ub + q)) = v;
-    }
+// 8 bits -> 8 E2M1 nibbles (1.0 = 0x2) or 0; bit t lands in nibble t (low nibble first).
+__device__ __forceinline__ uint32_t byte_to_e2m1(uint32_t b) {
+    uint32_t x = b & 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x << 1;
 }
 
-// Expand the 128 bytes of one operand row (used by the one-hot builder).
-template <bool kFp8>
-__device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint32_t* w) {
-    if (kFp8) {
-        store_units<true>(tile, r, 0, w[0], w[1]);
-        store_units<true>(tile, r, 4, w[2], w[3]);
+// One 16-byte operand unit from its sample bits: 32 samples (E2M1), 16 (E4M3) or 8 (FP16).
+template <int kKind>
+__device__ __forceinline__ uint4 unit_of_bits(uint32_t b) {
+    uint4 v;
+    if (kKind == kKindE2M1) {
+        v.x = byte_to_e2m1(b);
+        v.y = byte_to_e2m1(b >> 8);
+        v.z = byte_to_e2m1(b >> 16);
+        v.w = byte_to_e2m1(b >> 24);
+    } else if (kKind == kKindE4M3) {
+        v.x = nib_to_bytes(b & 0xF, 0x38u);
+        v.y = nib_to_bytes((b >> 4) & 0xF, 0x38u);
+        v.z = nib_to_bytes((b >> 8) & 0xF, 0x38u);
+        v.w = nib_to_bytes((b >> 12) & 0xF, 0x38u);
     } else {
-        store_units<false>(tile, r, 0, w[0], 0);
-        store_units<false>(tile, r, 4, w[1], 0);
+        v.x = bits2_to_h2(b & 3);
+        v.y = bits2_to_h2((b >> 2) & 3);
+        v.z = bits2_to_h2((b >> 4) & 3);
+        v.w = bits2_to_h2((b >> 6) & 3);
+    }
+    return v;
+}
+
+// Sample bits of one-hot row (c, p, m) for K-step ks, 32 per word in sample order (w[0..7];
+// words past the step, the class or the SNPs stay 0).
+template <int kKind>
+__device__ __forceinline__ void step_words(const Planes& pl, int c, int p, int m, int ks,
+                                           uint32_t* w) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) w[t] = 0;
+    if (m >= pl.M) return;
+    const uint4* row = pl.planes + pl.coff[c] + (size_t)p * pl.W4[c] * pl.M + m;
+    if (kKind == kKindE2M1) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int w4 = 2 * ks + hh;
+            if (w4 < pl.W4[c]) {
+                const uint4 g = __ldg(row + (size_t)w4 * pl.M);
+                w[4 * hh] = g.x; w[4 * hh + 1] = g.y; w[4 * hh + 2] = g.z; w[4 * hh + 3] = g.w;
+            }
+        }
+    } else if (kKind == kKindE4M3) {
+        if (ks < pl.W4[c]) {
+            const uint4 g = __ldg(row + (size_t)ks * pl.M);
+            w[0] = g.x; w[1] = g.y; w[2] = g.z; w[3] = g.w;
+        }
+    } else if ((ks >> 1) < pl.W4[c]) {
+        const uint4 g = __ldg(row + (size_t)(ks >> 1) * pl.M);
+        w[0] = (ks & 1) ? g.z : g.x;
+        w[1] = (ks & 1) ? g.w : g.y;
     }
 }
 
-template <bool kFp8>
-__device__ __forceinline__ uint4 step_bits(const Planes& pl, int c, int p, int m, int ks) {
-    if (m >= pl.M) return make_uint4(0, 0, 0, 0);
-    const int w4 = kFp8 ? ks : (ks >> 1);
-    const uint4 g = __ldg(pl.planes + pl.coff[c] + ((size_t)p * pl.W4[c] + w4) * pl.M + m);
-    if (kFp8) return g;
-    return (ks & 1) ? make_uint4(g.z, g.w, 0, 0) : make_uint4(g.x, g.y, 0, 0);
+// The 128 bytes of one operand row (r of the chunk) in the 128B-swizzled image.
+template <int kKind>
+__device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint32_t* w) {
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+        uint32_t b;
+        if (kKind == kKindE2M1) b = w[u];
+        else if (kKind == kKindE4M3) b = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
+        else b = (w[u >> 2] >> ((u & 3) * 8)) & 0xFFu;
+        *reinterpret_cast<uint4*>(tile + sw128_off(r, u)) = unit_of_bits<kKind>(b);
+    }
 }
 
 __device__ void sort_cands_epi(Cand* buf, int tid) {
@@ -344,7 +390,7 @@ __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds
     cursor_load(cu, cds, tiles, my_tiles);
 }
 
-template <bool kFp8>
+template <int kKind>
 __global__ void __launch_bounds__(kThreads, 1)
 scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
                 unsigned long long* __restrict__ prof) {
@@ -359,26 +405,34 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
     uint8_t* base = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* sK = base;                                    // [kStages][16 KB] third-SNP rows
-    uint8_t* sY = base + kStages * kChunk;                 // [kStages][8 KB]
-    uint8_t* sX = sY + kStages * kYChunk;                  // [kStages][256 B]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sX + kStages * kXBytes);
-    // bars: fullA[kStages], fullB[kStages], empty[kStages], acc_full[2], reg_free[3], drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 6);
+    constexpr int kTm = tm_stages<kKind>();
+    uint8_t* sK = base;                                    // [kSmStages][16 KB] third-SNP rows
+    uint8_t* sY = base + kSmStages * kChunk;               // [kSmStages][8 KB]
+    uint8_t* sX = sY + kSmStages * kYChunk;                // [kSmStages][256 B]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sX + kSmStages * kXBytes);
+    // bars: fullS[kSmStages], emptyS[kSmStages] (shared-memory ring), fullT[4], emptyT[4]
+    // (tensor-memory A ring), acc_full[2], reg_free[3], drain
+    constexpr int kNBars = 2 * kSmStages + 2 * kTmStagesMax + 6;
+    static_assert(kNBars * 8 + 8 <= 256, "barrier area");
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNBars);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     EpiShared& es = *reinterpret_cast<EpiShared*>(reinterpret_cast<uint8_t*>(bars) + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t fullA0 = smem_u32(bars), fullB0 = smem_u32(bars + kStages),
-                   empty0 = smem_u32(bars + 2 * kStages), accF0 = smem_u32(bars + 3 * kStages),
-                   regE0 = smem_u32(bars + 3 * kStages + 2),
-                   drain0 = smem_u32(bars + 3 * kStages + 5);
+    const uint32_t fullS0 = smem_u32(bars), emptyS0 = smem_u32(bars + kSmStages),
+                   fullT0 = smem_u32(bars + 2 * kSmStages),
+                   emptyT0 = smem_u32(bars + 2 * kSmStages + kTmStagesMax),
+                   accF0 = smem_u32(bars + 2 * kSmStages + 2 * kTmStagesMax),
+                   regE0 = accF0 + 16, drain0 = accF0 + 40;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(fullA0 + 8 * s, 1);
-            mbar_init(fullB0 + 8 * s, kProdThreads);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int s = 0; s < kSmStages; ++s) {
+            mbar_init(fullS0 + 8 * s, 1);
+            mbar_init(emptyS0 + 8 * s, 1);
+        }
+        for (int s = 0; s < kTmStagesMax; ++s) {
+            mbar_init(fullT0 + 8 * s, kProdThreads);
+            mbar_init(emptyT0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) mbar_init(accF0 + 8 * b, 1);
         for (int r = 0; r < kRegions; ++r) mbar_init(regE0 + 8 * r, kEpiWarps);
@@ -415,9 +469,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             cursor_load(cu, cds, tiles, my_tiles);
             long long q = 0;
             for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
-                const int s = (int)(q % kStages);
-                const unsigned ph = (unsigned)((q / kStages) & 1);
-                if (!mbar_wait_t(empty0 + 8 * s, ph ^ 1u, abort_flag, my_acc)) {
+                const int s = (int)(q % kSmStages);
+                const unsigned ph = (unsigned)((q / kSmStages) & 1);
+                if (!mbar_wait_t(emptyS0 + 8 * s, ph ^ 1u, abort_flag, my_acc)) {
                     fail(cu.cd);
                     break;
                 }
@@ -431,18 +485,19 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 const long long cy = base_c + (long long)(cu.tile.y >> 1) * nks + cu.ks;
                 const long long cx = base_c + (long long)(cu.tile.x >> 6) * nks + cu.ks;
                 const uint32_t xr = 2u * (uint32_t)(cu.tile.x & 63);
-                mbar_arrive_tx(fullA0 + 8 * s, kChunk + kYChunk + kXBytes);
-                bulk_g2s(smem_u32(sK + s * kChunk), oh + ca * kChunk, kChunk, fullA0 + 8 * s);
+                const uint32_t fb = fullS0 + 8 * s;
+                mbar_arrive_tx(fb, kChunk + kYChunk + kXBytes);
+                bulk_g2s(smem_u32(sK + s * kChunk), oh + ca * kChunk, kChunk, fb);
                 bulk_g2s(smem_u32(sY + s * kYChunk), oh + cy * kChunk + (cu.tile.y & 1) * kYChunk,
-                         kYChunk, fullA0 + 8 * s);
+                         kYChunk, fb);
                 bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
-                         kXBytes, fullA0 + 8 * s);
+                         kXBytes, fb);
             }
             // drain: the copies of the last stages issued must land before the CTA exits
-            for (long long d = (q > kStages ? q - kStages : 0); d < q; ++d) {
-                const int s = (int)(d % kStages);
+            for (long long d = (q > kSmStages ? q - kSmStages : 0); d < q; ++d) {
+                const int s = (int)(d % kSmStages);
                 volatile int no_abort = 0;
-                mbar_wait(fullA0 + 8 * s, (unsigned)((d / kStages) & 1), &no_abort);
+                mbar_wait(fullS0 + 8 * s, (unsigned)((d / kSmStages) & 1), &no_abort);
             }
         }
     } else if (warp == kWarpMma) {
@@ -471,22 +526,25 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)r * 128u;
                     for (int ks = 0; ks < KS[c]; ++ks, ++q) {
-                        const int s = (int)(q % kStages);
-                        const unsigned ph = (unsigned)((q / kStages) & 1);
-                        if (!mbar_wait_t(fullA0 + 8 * s, ph, abort_flag, my_acc) ||
-                            !mbar_wait_t(fullB0 + 8 * s, ph, abort_flag, my_acc)) {
+                        const int s = (int)(q % kSmStages), t = (int)(q % kTm);
+                        if (!mbar_wait_t(fullS0 + 8 * s, (unsigned)((q / kSmStages) & 1), abort_flag,
+                                         my_acc) ||
+                            !mbar_wait_t(fullT0 + 8 * t, (unsigned)((q / kTm) & 1), abort_flag,
+                                         my_acc)) {
                             fail(cd);
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t ta = tmem + kProdCol0 + (uint32_t)s * kProdCols;
+                        const uint32_t ta = tmem + kProdCol0 + (uint32_t)t * kProdCols;
                         const uint64_t db = sw128_desc(smem_u32(sK + s * kChunk));
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
-                            tc_mma_ts<kFp8>(d, ta + 8 * kk, db + 2 * kk, kIdesc,
-                                            (ks > 0 || kk > 0) ? 1u : 0u);
-                        tc_commit(empty0 + 8 * s);
+                            tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(),
+                                             (ks > 0 || kk > 0) ? 1u : 0u, tmem + kSfCol,
+                                             tmem + kSfCol + 16);
+                        tc_commit(emptyS0 + 8 * s);
+                        tc_commit(emptyT0 + 8 * t);
                     }
                 }
                 if (ok) tc_commit(accF0 + 8 * (int)(tl & 1));
@@ -498,26 +556,36 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         }
     } else if (warp >= kProdWarp0) {
         // ------------------------------------------------ producers: TMEM lane L = (jj, a, b)
-        // Product row (j, a, b) = one-hot row (j, b) AND one-hot row (i, a), byte by byte (0x38
-        // & 0x38 = 0x38 for E4M3 1.0; 0x3C00 & 0x3C00 for FP16), read from the staged Y and X
-        // rows (swizzled) and stored in natural K order into this stage's TMEM columns, where
+        // Product row (j, a, b) = one-hot row (j, b) AND one-hot row (i, a), bit by bit (an
+        // element is 1.0 or 0 in every kind, and 1.0 AND 1.0 = 1.0), read from the staged Y and
+        // X rows (swizzled) and stored in natural K order into this step's TMEM columns, where
         // the MMA reads it as its A operand.
         const int L = 32 * (warp & 3) + lane;
         const int jj = L >> 2, ga = (L >> 1) & 1, gb = L & 1;
         const uint32_t yr = (uint32_t)(2 * jj + gb);
-        const uint32_t tl_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kProdCol0;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        const uint32_t tl_base = tmem + lane_off + kProdCol0;
+        if (kKind == kKindE2M1) {
+            // block scale factors 2^0 (UE8M0 127) in every byte of the scale columns; ordered
+            // before the first MMA by this warp's first fullT arrival
+            uint32_t one[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) one[t] = 0x7F7F7F7Fu;
+            tc_st32(tmem + lane_off + kSfCol, one);
+            tc_wait_st();
+        }
         StepCursor cc{};
         cc.tl = 0;
         cursor_load(cc, cds, tiles, my_tiles);
         bool ok = true;
         long long q = 0;
         for (; cc.valid && ok; ++q, cursor_next(cc, cds, tiles, my_tiles)) {
-            const int s = (int)(q % kStages);
-            const unsigned ph = (unsigned)((q / kStages) & 1);
-            // the MMAs of step q - kStages have read this stage's TMEM columns; the loader's
-            // copies of step q have landed
-            const bool got = mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag) &&
-                             mbar_wait_t(fullA0 + 8 * s, ph, abort_flag, my_acc);
+            const int s = (int)(q % kSmStages), t = (int)(q % kTm);
+            // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of step q
+            // have landed
+            const bool got =
+                mbar_wait(emptyT0 + 8 * t, (unsigned)((q / kTm) & 1) ^ 1u, abort_flag) &&
+                mbar_wait_t(fullS0 + 8 * s, (unsigned)((q / kSmStages) & 1), abort_flag, my_acc);
             // tcgen05.st is warp-collective: the whole warp goes on or stops together
             if (!__all_sync(0xffffffffu, got)) {
                 fail(cc.cd);
@@ -538,10 +606,10 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 v[4 * u + 2] = y.z & x.z;
                 v[4 * u + 3] = y.w & x.w;
             }
-            tc_st32(tl_base + (uint32_t)s * kProdCols, v);
+            tc_st32(tl_base + (uint32_t)t * kProdCols, v);
             tc_wait_st();
             tc_fence_before();
-            mbar_arrive(fullB0 + 8 * s);
+            mbar_arrive(fullT0 + 8 * t);
         }
     } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue (warps 2..9)
@@ -707,9 +775,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     }
 }
 
-// Pre-tiled one-hot A chunks: chunk (c, kb, ks) holds rows r = 2 kk + z (third SNP
+// Pre-tiled one-hot chunks: chunk (c, kb, ks) holds rows r = 2 kk + z (third SNP
 // 64 kb + kk, genotype z) over the K-step's samples, already in the swizzled image.
-template <bool kFp8>
+template <int kKind>
 __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off1, int KS0, int KS1,
                               int kb_count) {
     const long long total = ((long long)kb_count * (KS0 + KS1)) * 128;
@@ -729,48 +797,53 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
             ks = (int)(q % KS1);
         }
         const int m = kb * kKB + (r >> 1), p = r & 1;
-        const uint4 g = step_bits<kFp8>(pl, c, p, m, ks);
-        const uint32_t w[4] = {g.x, g.y, g.z, g.w};
+        uint32_t w[8];
+        step_words<kKind>(pl, c, p, m, ks, w);
         uint8_t* tile = oh + (c ? off1 + (long long)kb * KS1 + ks : (long long)kb * KS0 + ks) * kChunk;
-        store_row<kFp8>(tile, (uint32_t)r, w);
+        store_row<kKind>(tile, (uint32_t)r, w);
     }
 }
 
 }  // namespace
 
 size_t scan_mma_smem() {
-    return 1024 + kStages * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 64;
+    return 1024 + kSmStages * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 64;
 }
 
-int mma_samples_per_step(bool fp8) { return fp8 ? 128 : 64; }
+int mma_samples_per_step(int kind) {
+    return kind == kKindE2M1 ? 256 : (kind == kKindE4M3 ? 128 : 64);
+}
 
 cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
-                          int kb_count, bool fp8, cudaStream_t st) {
+                          int kb_count, int kind, cudaStream_t st) {
     const long long total = ((long long)kb_count * (KS0 + KS1)) * 128;
     const int blocks = (int)((total + 255) / 256 < 65535 * 8 ? (total + 255) / 256 : 65535 * 8);
     if (total == 0) return cudaSuccess;
-    if (fp8) onehot_kernel<true><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
-    else onehot_kernel<false><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
+    if (kind == kKindE2M1)
+        onehot_kernel<kKindE2M1><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
+    else if (kind == kKindE4M3)
+        onehot_kernel<kKindE4M3><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
+    else
+        onehot_kernel<kKindF16><<<blocks, 256, 0, st>>>(pl, oh, off1, KS0, KS1, kb_count);
+    return cudaGetLastError();
+}
+
+template <int kKind>
+static cudaError_t launch_kind(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
+                               int grid, cudaStream_t st, unsigned long long* prof) {
+    const size_t smem = scan_mma_smem();
+    const cudaError_t e = cudaFuncSetAttribute(
+        scan_mma_kernel<kKind>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    scan_mma_kernel<kKind><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                            bool fp8, int grid, cudaStream_t st, unsigned long long* prof) {
-    const size_t smem = scan_mma_smem();
-    cudaError_t e;
-
-    if (fp8) {
-        e = cudaFuncSetAttribute(scan_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        scan_mma_kernel<true><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
-    } else {
-        e = cudaFuncSetAttribute(scan_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        scan_mma_kernel<false><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
-    }
-    return cudaGetLastError();
+                            int kind, int grid, cudaStream_t st, unsigned long long* prof) {
+    if (kind == kKindE2M1) return launch_kind<kKindE2M1>(cohorts, tiles, n_tiles, grid, st, prof);
+    if (kind == kKindE4M3) return launch_kind<kKindE4M3>(cohorts, tiles, n_tiles, grid, st, prof);
+    return launch_kind<kKindF16>(cohorts, tiles, n_tiles, grid, st, prof);
 }
 
 }  // namespace epi3

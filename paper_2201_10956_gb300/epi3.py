@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libepi3.so")
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OVERFLOW = -1, -2, -3, -4, -5, -6
 DEVICE_PTRS = 1
-PATH_AUTO, PATH_POPC, PATH_POPC8, PATH_MMA, PATH_MMA16 = 0, 1, 2, 3, 4
+PATH_AUTO, PATH_POPC, PATH_POPC8, PATH_MMA, PATH_MMA16, PATH_MMA4 = 0, 1, 2, 3, 4, 5
 MAX_TOPK = 512
 
 # Every symbol the header declares; tests check the library exports all of them.

@@ -41,7 +41,7 @@ def test_batch_matches_oracle(monkeypatch, force):
     with epi.Batch(data) as b:
         paths = b.paths()
         if force:
-            want = epi.PATH_MMA if force == "mma" else epi.PATH_POPC8
+            want = epi.PATH_MMA4 if force == "mma" else epi.PATH_POPC8
             assert np.all(paths == want)
         for rep in range(2):  # the second scan replays the captured graph
             tr, sc = b.scan(k)
@@ -83,7 +83,7 @@ def test_batch_config_48_cohorts():
     with epi.Batch(data) as b:
         tr, sc = b.scan(5)
         paths = b.paths()
-    assert set(paths.tolist()) <= {epi.PATH_MMA, epi.PATH_POPC8}
+    assert set(paths.tolist()) <= {epi.PATH_MMA4, epi.PATH_POPC8}
     for c, d in enumerate(cohorts):
         # the oracle rescores the answer exactly, and the single-handle scan agrees
         assert np.array_equal(oracle.scores(d.genotypes, d.phenotype, tr[c]), sc[c])

@@ -18,7 +18,8 @@ import paper_2201_10956_gb300 as epi
 pytestmark = pytest.mark.gpu
 
 KERNEL_PATHS = [("popc", epi.PATH_POPC), ("popc8", epi.PATH_POPC8), ("mma", epi.PATH_MMA),
-                ("mma16", epi.PATH_MMA16)]
+                ("mma16", epi.PATH_MMA16), ("mma4", epi.PATH_MMA4)]
+TENSOR = {"mma": epi.PATH_MMA, "mma16": epi.PATH_MMA16, "mma4": epi.PATH_MMA4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -76,18 +77,18 @@ def test_tensor_counts_exact_at_large_counts(name, path_id):
     assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
 
 
-@pytest.mark.parametrize("name", ["mma", "mma16"])
+@pytest.mark.parametrize("name", sorted(TENSOR))
 def test_tensor_scan_tiny_config(name):
     d = gen.make_config("tiny")
     with epi.Handle(d.genotypes, d.phenotype) as h:
         h.set_option("path", name)
         tr, sc = h.scan(10)
-        assert h.stats()["path"] == (epi.PATH_MMA if name == "mma" else epi.PATH_MMA16)
+        assert h.stats()["path"] == TENSOR[name]
     otr, osc, _ = oracle.scan_topk(d.genotypes, d.phenotype, 10)
     assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
 
 
-@pytest.mark.parametrize("name", ["mma", "mma16"])
+@pytest.mark.parametrize("name", sorted(TENSOR))
 def test_tensor_scan_range_slices(name):
     g, ph = pins.tiny_data(90, 400, 170, seed=19)
     k = 9
@@ -103,7 +104,7 @@ def test_tensor_scan_range_slices(name):
         assert [r[1:] for r in rows[:k]] == [tuple(map(int, t)) for t in full_t]
 
 
-@pytest.mark.parametrize("name", ["mma", "mma16"])
+@pytest.mark.parametrize("name", sorted(TENSOR))
 def test_tensor_scan_medium_sampled(name):
     d = gen.make_config("medium")
     g, ph = d.genotypes, d.phenotype
@@ -116,12 +117,13 @@ def test_tensor_scan_medium_sampled(name):
     assert np.array_equal(oracle.scores(g, ph, tr), sc)
 
 
-def test_bounded_wait_times_out_and_context_survives(monkeypatch):
+@pytest.mark.parametrize("name", ["mma", "mma4"])
+def test_bounded_wait_times_out_and_context_survives(monkeypatch, name):
     # a device wait that can only run out: the kernel must report EPI3_ERR_TIMEOUT after its
     # 1 s limit, release its resources, and leave the context usable
     g, ph = pins.tiny_data(40, 300, 120, seed=77)
     with epi.Handle(g, ph) as h:
-        h.set_option("path", "mma")
+        h.set_option("path", name)
         monkeypatch.setenv("EPI3_FAULT", "timeout")
         with pytest.raises(epi.Epi3Error) as ei:
             h.scan(5)
