@@ -345,7 +345,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     torch.cuda.set_device(local_rank)
     B.build()
-    d = gen.make_config(args.config, seed=args.seed)
+    d = gen.make_config(args.config, seed=args.seed, n_snps=args.snps)
     m, n, k = d.n_snps, d.n_samples, d.top_k
     pb, pe = shard_pairs(m, world, rank)
     stream = torch.cuda.Stream()
@@ -448,7 +448,8 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": DTYPES[st["path"]],
             "data": "synthetic",
-            "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "path": args.path,
+            "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}"
+                       + (f" (SNP count overridden: {m})" if args.snps else ""), "path": args.path,
                        "top_k": k, "l2": "flushed before every timed step (512 MB write)",
                        "wall_s": wall},
             "gpu_launches": st["kernel_launches"] * args.steps,
@@ -468,6 +469,8 @@ def main():
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="large")
     ap.add_argument("--path", default="auto")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--snps", type=int, default=None,
+                    help="another SNP count for the workload (a smaller case for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -144,9 +144,12 @@ CONFIGS = {
 }
 
 
-def make_config(name: str, seed: int = 1) -> Dataset:
-    """One of the named single-cohort workloads: tiny, medium, large, stress."""
+def make_config(name: str, seed: int = 1, n_snps: int | None = None) -> Dataset:
+    """One of the named single-cohort workloads: tiny, medium, large, stress (optionally
+    with another SNP count, everything else kept: a smaller case of the same shape)."""
     c = dict(CONFIGS[name])
+    if n_snps is not None:
+        c["n_snps"] = int(n_snps)
     frac = c.pop("case_fraction")
     n1 = int(round(frac * c["n_samples"]))
     return make_dataset(n_cases=n1, seed=seed, name=name, **c)

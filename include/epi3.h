@@ -174,9 +174,12 @@ typedef struct {
     float k2_rel_bound;      /* proven |FP32 - FP64| bound: rel * K2 + abs */
     float k2_abs_bound;
     /* tensor-core scan with option "profile" = 1: share of the kernel's cycles each role
-       spent waiting (A loader on free stages, MMA issuer on full stages, MMA issuer on free
-       accumulators, producer warps on free stages, epilogue warps on full accumulators) */
+       spent waiting (operand loader on free shared-memory stages, MMA issuer on full stages,
+       MMA issuer on free accumulators, producer warps on loaded stages, epilogue warps on
+       full accumulators, producer warps on free tensor-memory stages) and the share the MMA
+       issuer spent issuing tcgen05.mma / commit instructions */
     float wait_loader, wait_mma_operands, wait_mma_accum, wait_producers, wait_epilogue;
+    float wait_producers_tmem, mma_issue;
 } epi3_stats;
 
 int epi3_get_stats(const epi3_handle* h, epi3_stats* out);

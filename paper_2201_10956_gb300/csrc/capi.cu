@@ -467,6 +467,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.block = 448;
     s.kernel_launches = 5;
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
+    s.wait_producers_tmem = s.mma_issue = 0.f;
     if (h->profile && h->d_prof) {
         unsigned long long p[8];
         CK(cudaMemcpy(p, h->d_prof, sizeof(p), cudaMemcpyDeviceToHost), "read profile");
@@ -474,8 +475,10 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
         s.wait_loader = (float)(p[0] / tot);
         s.wait_mma_operands = (float)(p[1] / tot);
         s.wait_mma_accum = (float)(p[2] / tot);
-        s.wait_producers = (float)(p[3] / (tot * 8));
+        s.wait_producers = (float)(p[3] / (tot * 4));
         s.wait_epilogue = (float)(p[4] / (tot * 8));
+        s.wait_producers_tmem = (float)(p[6] / (tot * 4));
+        s.mma_issue = (float)(p[7] / tot);
     }
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
@@ -1028,7 +1031,8 @@ int batch_capture(epi3_batch* b, int top_k) {
     }
     cur = "tensor scan";
     cur_c = -1;
-    if (b->n_tiles > 0) ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, kKindE2M1, b->sm_count, b->stream));
+    if (b->n_tiles > 0)
+        ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, kKindE2M1, b->sm_count, b->stream));
     cur = "popc8 scan";
     for (int c = 0; c < b->n; ++c) {
         if (b->path[c] != EPI3_PATH_POPC8) continue;

@@ -57,7 +57,7 @@ static_assert(kRegions * 128 + 4 * kProdCols <= kTmemCols, "tensor memory budget
 static_assert(kRegions * 128 + 3 * kProdCols <= kSfCol, "tensor memory budget (E2M1)");
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
 constexpr int kCandCapMma = 1024;
-constexpr int kRoundMax = 2 * kEpiThreads;   // appends per epilogue round at most
+constexpr int kPruneAt = kCandCapMma / 2;   // local candidates that trigger a prune
 
 
 // ------------------------------------------------------------------ PTX helpers
@@ -177,6 +177,15 @@ __device__ __forceinline__ void tc_wait_ld() {
 }
 __device__ __forceinline__ void epi_bar() {
     asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+}
+// Barrier of the epilogue threads that also returns whether any of them passed true.
+__device__ __forceinline__ bool epi_bar_or(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 1, %2, a;\n"
+        " selp.u32 %0, 1, 0, b;\n}\n"
+        : "=r"(r) : "r"((uint32_t)p), "r"(kEpiThreads) : "memory");
+    return r != 0;
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128B swizzle, rows of 128 bytes,
@@ -303,12 +312,13 @@ __device__ void sort_cands_epi(Cand* buf, int tid) {
 
 struct EpiShared {
     Cand buf[kCandCapMma];
-    int cnt, keep, stop;
+    int cnt, keep;
     float tloc;
 };
 
-// Sort the buffer, publish this CTA's band threshold, keep the entries inside the band;
-// spill to the global list when too many tie.  Called by all epilogue threads.
+// Sort the buffer (cnt <= kCandCapMma entries), publish this CTA's band threshold, keep the
+// entries inside the band; spill to the global list when too many tie.  Called by all
+// epilogue threads.
 __device__ int epi_prune(const CohortDev& a, EpiShared& es, int cnt, int tid, bool final_flush) {
     const float kInf = __int_as_float(0x7f800000);
     if (cnt >= a.top_k) {
@@ -341,7 +351,7 @@ __device__ int epi_prune(const CohortDev& a, EpiShared& es, int cnt, int tid, bo
     if (keep) atomicAdd(&es.keep, keep);
     epi_bar();
     int kept = es.keep;
-    if (kept > kCandCapMma - kRoundMax) {
+    if (kept > kPruneAt) {
         for (int idx = tid; idx < kept; idx += kEpiThreads) {
             const Cand e = es.buf[idx];
             const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
@@ -354,6 +364,13 @@ __device__ int epi_prune(const CohortDev& a, EpiShared& es, int cnt, int tid, bo
     return kept;
 }
 
+// A candidate straight to the cohort's global list (the local buffer is full).
+__device__ __forceinline__ void cand_global(const CohortDev& a, const Cand& e) {
+    const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
+    if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
+    else atomicOr(&a.ctrl->status, kStCandOverflow);
+}
+
 // Walks one CTA's sequence of (tile, class, K-step): tiles blockIdx.x + n * gridDim.x,
 // class 0 then class 1, K-steps of the tile's cohort (classes without samples skipped).
 struct StepCursor {
@@ -363,6 +380,18 @@ struct StepCursor {
     const CohortDev* cd;
     bool valid;
 };
+
+// Position in a ring of n stages: stage index and the parity of the current pass.
+struct Ring {
+    int s;
+    uint32_t ph;
+};
+__device__ __forceinline__ void ring_next(Ring& r, int n) {
+    if (++r.s == n) {
+        r.s = 0;
+        r.ph ^= 1u;
+    }
+}
 
 __device__ __forceinline__ void cursor_load(StepCursor& cu, const CohortDev* cds, const int4* tiles,
                                             long long my_tiles) {
@@ -397,9 +426,10 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     // prof (optional): per role, cycles spent waiting, summed over CTAs:
     //   [0] loader on empty stages, [1] MMA on full stages, [2] MMA on free accumulator
     //   regions, [3] producers (lane 0 of each producer warp) on full stages, [4] epilogue
-    //   (lane 0 of each epilogue warp) on full accumulators, [5] kernel cycles of this CTA
+    //   (lane 0 of each epilogue warp) on full accumulators, [5] kernel cycles of this CTA,
+    //   [6] producers on free tensor-memory stages, [7] MMA issuer issuing MMAs and commits
     const long long t_start = clock64();
-    unsigned long long w_acc = 0, busy = 0;
+    unsigned long long w_acc = 0, busy = 0, w_acc2 = 0;
     unsigned long long* my_acc = prof ? &w_acc : nullptr;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
@@ -439,7 +469,6 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         mbar_init(drain0, 1);
         *abort_flag = 0;
         es.cnt = 0;
-        es.stop = 0;
         es.tloc = __int_as_float(0x7f800000);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -468,10 +497,10 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             cu.tl = 0;
             cursor_load(cu, cds, tiles, my_tiles);
             long long q = 0;
+            Ring rs{0, 0u};
             for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
-                const int s = (int)(q % kSmStages);
-                const unsigned ph = (unsigned)((q / kSmStages) & 1);
-                if (!mbar_wait_t(emptyS0 + 8 * s, ph ^ 1u, abort_flag, my_acc)) {
+                const int s = rs.s;
+                if (!mbar_wait_t(emptyS0 + 8 * s, rs.ph ^ 1u, abort_flag, my_acc)) {
                     fail(cu.cd);
                     break;
                 }
@@ -492,6 +521,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                          kYChunk, fb);
                 bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
                          kXBytes, fb);
+                ring_next(rs, kSmStages);
             }
             // drain: the copies of the last stages issued must land before the CTA exits
             for (long long d = (q > kSmStages ? q - kSmStages : 0); d < q; ++d) {
@@ -503,48 +533,47 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     } else if (warp == kWarpMma) {
         // ------------------------------------------------ MMA issuer (lane 0)
         if (lane == 0) {
-            long long q = 0;
             bool ok = true;
             if (cds[0].inject_timeout) {  // test hook: a wait that can only run out (1 s)
                 if (!mbar_wait(drain0, 0, abort_flag)) fail(cds);
                 ok = false;
             }
+            Ring rS{0, 0u}, rT{0, 0u}, rR{0, 0u};
             for (long long tl = 0; tl < my_tiles && ok; ++tl) {
                 const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
                 const CohortDev* cd = cds + tile.w;
                 const int KS[2] = {cd->KS[0], cd->KS[1]};
                 for (int c = 0; c < 2 && ok; ++c) {
                     // accumulator region of segment (tile, class): a ring of kRegions
-                    const long long seg = 2 * tl + c;
-                    const int r = (int)(seg % kRegions);
-                    const unsigned use = (unsigned)((seg / kRegions) & 1);
-                    if (!mbar_wait_t(regE0 + 8 * r, use ^ 1u, abort_flag, prof ? &busy : nullptr)) {
+                    if (!mbar_wait_t(regE0 + 8 * rR.s, rR.ph ^ 1u, abort_flag, prof ? &busy : nullptr)) {
                         fail(cd);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)r * 128u;
-                    for (int ks = 0; ks < KS[c]; ++ks, ++q) {
-                        const int s = (int)(q % kSmStages), t = (int)(q % kTm);
-                        if (!mbar_wait_t(fullS0 + 8 * s, (unsigned)((q / kSmStages) & 1), abort_flag,
-                                         my_acc) ||
-                            !mbar_wait_t(fullT0 + 8 * t, (unsigned)((q / kTm) & 1), abort_flag,
-                                         my_acc)) {
+                    const uint32_t d = tmem + (uint32_t)rR.s * 128u;
+                    ring_next(rR, kRegions);
+                    for (int ks = 0; ks < KS[c]; ++ks) {
+                        if (!mbar_wait_t(fullS0 + 8 * rS.s, rS.ph, abort_flag, my_acc) ||
+                            !mbar_wait_t(fullT0 + 8 * rT.s, rT.ph, abort_flag, my_acc)) {
                             fail(cd);
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t ta = tmem + kProdCol0 + (uint32_t)t * kProdCols;
-                        const uint64_t db = sw128_desc(smem_u32(sK + s * kChunk));
+                        const long long t_issue = prof ? clock64() : 0;
+                        const uint32_t ta = tmem + kProdCol0 + (uint32_t)rT.s * kProdCols;
+                        const uint64_t db = sw128_desc(smem_u32(sK + rS.s * kChunk));
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
                             tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(),
                                              (ks > 0 || kk > 0) ? 1u : 0u, tmem + kSfCol,
                                              tmem + kSfCol + 16);
-                        tc_commit(emptyS0 + 8 * s);
-                        tc_commit(emptyT0 + 8 * t);
+                        tc_commit(emptyS0 + 8 * rS.s);
+                        tc_commit(emptyT0 + 8 * rT.s);
+                        if (prof) w_acc2 += (unsigned long long)(clock64() - t_issue);
+                        ring_next(rS, kSmStages);
+                        ring_next(rT, kTm);
                     }
                 }
                 if (ok) tc_commit(accF0 + 8 * (int)(tl & 1));
@@ -577,39 +606,54 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         StepCursor cc{};
         cc.tl = 0;
         cursor_load(cc, cds, tiles, my_tiles);
-        bool ok = true;
-        long long q = 0;
-        for (; cc.valid && ok; ++q, cursor_next(cc, cds, tiles, my_tiles)) {
-            const int s = (int)(q % kSmStages), t = (int)(q % kTm);
+        // Software pipeline: step q's shared-memory loads are issued before the wait for step
+        // q-1's tensor-memory store, so the two latencies overlap.
+        int t_prev = -1;  // TMEM stage of a store issued but not yet published
+        Ring rS{0, 0u}, rT{0, 0u};
+        for (; cc.valid; cursor_next(cc, cds, tiles, my_tiles)) {
+            const int s = rS.s, t = rT.s;
             // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of step q
             // have landed
             const bool got =
-                mbar_wait(emptyT0 + 8 * t, (unsigned)((q / kTm) & 1) ^ 1u, abort_flag) &&
-                mbar_wait_t(fullS0 + 8 * s, (unsigned)((q / kSmStages) & 1), abort_flag, my_acc);
+                mbar_wait_t(emptyT0 + 8 * t, rT.ph ^ 1u, abort_flag, prof ? &w_acc2 : nullptr) &&
+                mbar_wait_t(fullS0 + 8 * s, rS.ph, abort_flag, my_acc);
             // tcgen05.st is warp-collective: the whole warp goes on or stops together
             if (!__all_sync(0xffffffffu, got)) {
                 fail(cc.cd);
-                ok = false;
                 break;
             }
             tc_fence_after();
             const uint32_t xp = (2u * (uint32_t)(cc.tile.x & 63) + (uint32_t)ga) & 7u;
             const uint8_t* ys = sY + s * kYChunk;
             const uint8_t* xs = sX + s * kXBytes + ga * 128;
+            uint4 y[8], x[8];
+#pragma unroll
+            for (uint32_t u = 0; u < 8; ++u) {
+                y[u] = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
+                x[u] = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
+            }
+            if (t_prev >= 0) {  // publish step q-1
+                tc_wait_st();
+                tc_fence_before();
+                mbar_arrive(fullT0 + 8 * t_prev);
+            }
             uint32_t v[32];
 #pragma unroll
             for (uint32_t u = 0; u < 8; ++u) {
-                const uint4 y = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
-                const uint4 x = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
-                v[4 * u + 0] = y.x & x.x;
-                v[4 * u + 1] = y.y & x.y;
-                v[4 * u + 2] = y.z & x.z;
-                v[4 * u + 3] = y.w & x.w;
+                v[4 * u + 0] = y[u].x & x[u].x;
+                v[4 * u + 1] = y[u].y & x[u].y;
+                v[4 * u + 2] = y[u].z & x[u].z;
+                v[4 * u + 3] = y[u].w & x[u].w;
             }
             tc_st32(tl_base + (uint32_t)t * kProdCols, v);
+            t_prev = t;
+            ring_next(rS, kSmStages);
+            ring_next(rT, kTm);
+        }
+        if (t_prev >= 0) {  // the last store (also on the abort path: nothing left in flight)
             tc_wait_st();
             tc_fence_before();
-            mbar_arrive(fullT0 + 8 * t);
+            mbar_arrive(fullT0 + 8 * t_prev);
         }
     } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue (warps 2..9)
@@ -621,32 +665,28 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         const int jj = 8 * quad + (lane >> 2), me = lane & 3;
         const int h1 = me >> 1, l0 = me & 1;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        int cnt = 0, cur = -1;
-        bool ok = true;
-        for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+        int cur = -1;
+        Ring rR{0, 0u};
+        for (long long tl = 0; tl < my_tiles; ++tl) {
             const int buf = (int)(tl & 1);
             const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
             const CohortDev& cd = cds[tile.w];
             if (tile.w != cur) {  // candidates are per cohort: flush the previous one's
-                if (cur >= 0) cnt = epi_prune(cds[cur], es, cnt, tid, true);
+                epi_bar();  // the previous tile's count is settled
+                if (cur >= 0) epi_prune(cds[cur], es, min(es.cnt, kCandCapMma), tid, true);
                 if (tid == 0) {
                     es.cnt = 0;
                     es.tloc = __int_as_float(0x7f800000);
                 }
-                epi_bar();
-                cnt = 0;
                 cur = tile.w;
             }
             const int M = cd.pl.M;
             const int i = tile.x, j = tile.y * kJB + jj, kb0 = tile.z * kKB;
-            if (!mbar_wait_t(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag, my_acc)) fail(&cd);
-            epi_bar();  // uniform decision: every epilogue thread stops on the same tile
-            if (tid == 0) es.stop = *abort_flag;
-            epi_bar();
-            if (es.stop) {
-                ok = false;
-                break;
-            }
+            bool bad = !mbar_wait_t(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag, my_acc);
+            if (bad) fail(&cd);
+            // uniform decision (every epilogue thread stops on the same tile); also orders the
+            // previous tile's candidate bookkeeping before this tile's appends
+            if (epi_bar_or(bad || *abort_flag)) break;
             tc_fence_after();
             const int KS0 = cd.KS[0], KS1 = cd.KS[1];
             const PairTables pt = cd.pt;
@@ -666,10 +706,19 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             }
             mx[0] = __ldg(pt.marg + i);
             mx[1] = __ldg(pt.marg + M + i);
-            const uint32_t rc[2] = {(uint32_t)((2 * tl) % kRegions) * 128u,
-                                    (uint32_t)((2 * tl + 1) % kRegions) * 128u};
+            const int reg0 = rR.s;
+            ring_next(rR, kRegions);
+            const int reg1 = rR.s;
+            ring_next(rR, kRegions);
+            const uint32_t rc[2] = {(uint32_t)reg0 * 128u, (uint32_t)reg1 * 128u};
+            const float2* lf2 = cd.k2.lf2;
+            float* dbg = cd.dbg;
+            Ctrl* ctrl = cd.ctrl;
             for (int gi = 0; gi < 4; ++gi) {
                 const int g = half + 2 * gi;            // 16-column group = 8 third SNPs
+                // the global band threshold only shrinks: a copy read once per group is a
+                // valid (looser) filter
+                const float thr_g = __uint_as_float(*(volatile unsigned*)&ctrl->thr);
                 uint32_t v[2][16];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) tc_ld16(tmem + lane_base + rc[c] + 16 * g, v[c]);
@@ -728,33 +777,35 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
 #pragma unroll
                     for (int q = 0; q < kCells; ++q) neg |= r0[q] | r1[q];
                     if (neg < 0) {
-                        atomicOr(&cd.ctrl->status, kStBadCount);
+                        atomicOr(&ctrl->status, kStBadCount);
                         continue;
                     }
-                    const float s = k2_f32(r0, r1, cd.k2.lf2);
-                    if (cd.dbg) cd.dbg[((size_t)i * M + j) * M + k] = s;
-                    if (s <= fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&cd.ctrl->thr))) {
+                    const float s = k2_f32(r0, r1, lf2);
+                    if (dbg) dbg[((size_t)i * M + j) * M + k] = s;
+                    if (s <= fminf(es.tloc, thr_g)) {
                         const int idx = atomicAdd(&es.cnt, 1);
-                        es.buf[idx] = Cand{s, i, j, k};
+                        if (idx < kCandCapMma) es.buf[idx] = Cand{s, i, j, k};
+                        else cand_global(cd, Cand{s, i, j, k});
                     }
                 }
-                epi_bar();
-                cnt = es.cnt;
-                epi_bar();
-                if (cnt > kCandCapMma - kRoundMax) {
-                    cnt = epi_prune(cd, es, cnt, tid, false);
-                    if (tid == 0) es.cnt = cnt;
-                    epi_bar();
-                }
             }
+            // accumulators read: release both regions to the MMA issuer
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(regE0 + 8 * (int)((2 * tl) % kRegions));
-                mbar_arrive(regE0 + 8 * (int)((2 * tl + 1) % kRegions));
+                mbar_arrive(regE0 + 8 * reg0);
+                mbar_arrive(regE0 + 8 * reg1);
+            }
+            epi_bar();  // every append of this tile is in
+            const int cnt = min(es.cnt, kCandCapMma);
+            if (cnt > kPruneAt) {  // uniform: every thread read the same count
+                epi_bar();
+                const int kept = epi_prune(cd, es, cnt, tid, false);
+                if (tid == 0) es.cnt = kept;
             }
         }
-        if (cur >= 0) epi_prune(cds[cur], es, cnt, tid, true);
+        epi_bar();
+        if (cur >= 0) epi_prune(cds[cur], es, min(es.cnt, kCandCapMma), tid, true);
     }
     if (prof) {
         const unsigned long long total = (unsigned long long)(clock64() - t_start);
@@ -762,8 +813,12 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         if (warp == kWarpMma && lane == 0) {
             atomicAdd(prof + 1, w_acc);
             atomicAdd(prof + 2, busy);
+            atomicAdd(prof + 7, w_acc2);
         }
-        if (warp >= kProdWarp0 && lane == 0) atomicAdd(prof + 3, w_acc);
+        if (warp >= kProdWarp0 && lane == 0) {
+            atomicAdd(prof + 3, w_acc);
+            atomicAdd(prof + 6, w_acc2);
+        }
         if (warp >= kEpiWarp0 && warp < kProdWarp0 && lane == 0) atomicAdd(prof + 4, w_acc);
         if (threadIdx.x == 0) atomicAdd(prof + 5, total);
     }
