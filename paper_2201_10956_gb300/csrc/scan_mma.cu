@@ -539,6 +539,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 ok = false;
             }
             Ring rS{0, 0u}, rT{0, 0u}, rR{0, 0u};
+            const uint64_t db0 = sw128_desc(smem_u32(sK));
             for (long long tl = 0; tl < my_tiles && ok; ++tl) {
                 const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
                 const CohortDev* cd = cds + tile.w;
@@ -554,8 +555,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     const uint32_t d = tmem + (uint32_t)rR.s * 128u;
                     ring_next(rR, kRegions);
                     for (int ks = 0; ks < KS[c]; ++ks) {
-                        if (!mbar_wait_t(fullS0 + 8 * rS.s, rS.ph, abort_flag, my_acc) ||
-                            !mbar_wait_t(fullT0 + 8 * rT.s, rT.ph, abort_flag, my_acc)) {
+                        // the producers arrive on fullT only after they saw the step's bulk
+                        // copies land (fullS), so one wait covers both operands
+                        if (!mbar_wait_t(fullT0 + 8 * rT.s, rT.ph, abort_flag, my_acc)) {
                             fail(cd);
                             ok = false;
                             break;
@@ -563,13 +565,14 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                         tc_fence_after();
                         const long long t_issue = prof ? clock64() : 0;
                         const uint32_t ta = tmem + kProdCol0 + (uint32_t)rT.s * kProdCols;
-                        const uint64_t db = sw128_desc(smem_u32(sK + rS.s * kChunk));
+                        const uint64_t db = db0 + (uint64_t)((rS.s * kChunk) >> 4);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
                             tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(),
                                              (ks > 0 || kk > 0) ? 1u : 0u, tmem + kSfCol,
                                              tmem + kSfCol + 16);
-                        tc_commit(emptyS0 + 8 * rS.s);
+                        // one commit per step: its arrival frees the TMEM A stage, and the
+                        // producers then release the shared-memory stage to the loader
                         tc_commit(emptyT0 + 8 * rT.s);
                         if (prof) w_acc2 += (unsigned long long)(clock64() - t_issue);
                         ring_next(rS, kSmStages);
@@ -610,6 +613,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         // q-1's tensor-memory store, so the two latencies overlap.
         int t_prev = -1;  // TMEM stage of a store issued but not yet published
         Ring rS{0, 0u}, rT{0, 0u};
+        Ring rF{0, 0u};   // shared-memory stage of step q - kTm (released once its MMAs finish)
+        int warm = 0;     // min(q, kTm)
         for (; cc.valid; cursor_next(cc, cds, tiles, my_tiles)) {
             const int s = rS.s, t = rT.s;
             // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of step q
@@ -623,6 +628,12 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 break;
             }
             tc_fence_after();
+            if (warm == kTm) {  // step q - kTm is complete: its K, Y, X stage goes back to the loader
+                if (warp == kProdWarp0 && lane == 0) mbar_arrive(emptyS0 + 8 * rF.s);
+                ring_next(rF, kSmStages);
+            } else {
+                ++warm;
+            }
             const uint32_t xp = (2u * (uint32_t)(cc.tile.x & 63) + (uint32_t)ga) & 7u;
             const uint8_t* ys = sY + s * kYChunk;
             const uint8_t* xs = sX + s * kXBytes + ga * 128;
