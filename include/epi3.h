@@ -180,6 +180,11 @@ typedef struct {
        issuer spent issuing tcgen05.mma / commit instructions */
     float wait_loader, wait_mma_operands, wait_mma_accum, wait_producers, wait_epilogue;
     float wait_producers_tmem, mma_issue;
+    /* tensor-core scan: a table whose approximate K2 (Stirling's form with the hardware log,
+       no table lookups) exceeds the candidate threshold by more than this proven bound is
+       skipped without its exact FP32 score; the bound comes from the approximation's error
+       measured on the device for every count 0..N+1 */
+    float k2_prune_bound;
 } epi3_stats;
 
 int epi3_get_stats(const epi3_handle* h, epi3_stats* out);

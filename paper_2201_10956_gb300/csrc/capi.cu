@@ -82,6 +82,7 @@ struct epi3_handle {
     double* d_lf64 = nullptr;
     K2Tables k2{};
     int g_bits = 0;
+    double approx_err = 0.0;      // measured max |lf_approx - lf| over 0..N+1
     Ctrl* d_ctrl = nullptr;
     Cand* d_cand = nullptr;
     long long cand_cap = 0;
@@ -181,13 +182,42 @@ int build_k2_tables(epi3_handle* h) {
        "upload lf64");
     CK(cudaMemcpyAsync(h->d_lf2, lf2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->stream),
        "upload lf2");
-    CK(cudaStreamSynchronize(h->stream), "sync lf upload");
     h->k2.lf2 = h->d_lf2;
     h->k2.lf64 = h->d_lf64;
     h->k2.rel = std::ldexp(1.0f, -23);
     h->k2.abs_ = std::ldexp(1.0f, -(g + 13));
+    // Pruning bound of the tensor scan: |k2_approx - s32| for any table of this data set.
+    //   delta  measured max of (n + 1/2) |lg2_hw(n+1) - log2(n+1)| over n = 0..N+1
+    //   Stirling remainders: at most 1/6 per cell (e(r+1) - e(r0) - e(r1), 0 < e <= 1/12)
+    //   FMA chain (81 steps, log2 units): each rounds by at most 2^-24 |acc|; every finished
+    //     cell adds a positive amount (its K2 term + ln(2 pi)/2 - Stirling remainder), so
+    //     0 <= acc <= (K + 27 (ln(2 pi)/2 + 1/12)) / ln2 + T + 81 delta, with K = 27 ln(N+2)
+    //     + N ln 2 bounding K2 and T = (N + 3/2) log2(N + 2) the largest single product
+    //   final FMA and the FP32 constants: 2^-22 (K + 27 ln(2 pi)/2 + ln2 (K/ln2 + T))
+    //   s32 against K2: rel * K + abs
+    // and the bound used is twice the sum plus 1/2 nat.
+    double* d_err = nullptr;
+    CK(dev_alloc((void**)&d_err, sizeof(double)), "alloc approx error");
+    double delta = 0.0;
+    cudaError_t ce = launch_approx_error(h->d_lf64, n, d_err, h->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(&delta, d_err, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    cudaFree(d_err);
+    CK(ce, "approx error");
+    const double u = std::ldexp(1.0, -24), ln2 = std::log(2.0);
+    const double kmax = 27.0 * std::log((double)h->N + 2.0) + (double)h->N * ln2;
+    const double tmax = ((double)h->N + 1.5) * std::log2((double)h->N + 2.0);
+    const double amax = (kmax + 27.0 * (0.9189385332046727 + 1.0 / 12.0)) / ln2 + tmax +
+                        81.0 * delta;
+    const double d_approx = 27.0 / 6.0 + ln2 * (81.0 * delta + 81.0 * u * amax) +
+                            4.0 * u * (kmax + 27.0 * 0.9189385332046727 + ln2 * amax);
+    const double d_s32 = (double)h->k2.rel * kmax + (double)h->k2.abs_;
+    h->k2.prune_delta = (float)(2.0 * (d_approx + d_s32) + 0.5);
+    h->approx_err = delta;
     h->stats.k2_rel_bound = h->k2.rel;
     h->stats.k2_abs_bound = h->k2.abs_;
+    h->stats.k2_prune_bound = h->k2.prune_delta;
     return EPI3_OK;
 }
 
@@ -482,6 +512,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     }
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
+    s.k2_prune_bound = h->k2.prune_delta;
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
@@ -605,6 +636,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     s.kernel_launches = 5;
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
+    s.k2_prune_bound = h->k2.prune_delta;
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);

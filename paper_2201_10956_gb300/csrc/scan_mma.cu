@@ -723,6 +723,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             ring_next(rR, kRegions);
             const uint32_t rc[2] = {(uint32_t)reg0 * 128u, (uint32_t)reg1 * 128u};
             const float2* lf2 = cd.k2.lf2;
+            const float prune = cd.k2.prune_delta;
             float* dbg = cd.dbg;
             Ctrl* ctrl = cd.ctrl;
             for (int gi = 0; gi < 4; ++gi) {
@@ -791,6 +792,11 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                         atomicOr(&ctrl->status, kStBadCount);
                         continue;
                     }
+                    // most tables lie far above the band: prove it from the table-free
+                    // approximation and skip the exact score's 81 log-table gathers
+                    if (!dbg && prune > 0.f &&
+                        __fsub_rn(k2_approx(r0, r1), prune) > fminf(es.tloc, thr_g))
+                        continue;
                     const float s = k2_f32(r0, r1, lf2);
                     if (dbg) dbg[((size_t)i * M + j) * M + k] = s;
                     if (s <= fminf(es.tloc, thr_g)) {

@@ -270,6 +270,30 @@ cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Largest error of the products (n + 1/2) * lg2_hw(n + 1) of k2_approx over every n the scan
+// can pass (0 .. N+1): the hardware log against FP64 log2, scaled by the exact multiplier.
+__global__ void approx_error_kernel(const double* __restrict__ lf64, int n,
+                                    unsigned long long* __restrict__ out) {
+    (void)lf64;
+    double e = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const float x = exact_float(t);
+        const double err = (double)lg2_hw(__fadd_rn(x, 1.f)) - log2((double)t + 1.0);
+        e = fmax(e, ((double)t + 0.5) * fabs(err));
+    }
+    // non-negative doubles order like their bit patterns
+    atomicMax(out, (unsigned long long)__double_as_longlong(e));
+}
+
+cudaError_t launch_approx_error(const double* lf64, int n_lf, double* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (n_lf + 255) / 256 < 1024 ? (n_lf + 255) / 256 : 1024;
+    approx_error_kernel<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(
+        lf64, n_lf, reinterpret_cast<unsigned long long*>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_select(Ctrl* ctrl, const Cand* cand, long long cap, int top_k, float rel,
                           float abs_, cudaStream_t st) {
     select_kernel<<<1, kSelThreads, 0, st>>>(ctrl, cand, cap, top_k, rel, abs_);
