@@ -46,7 +46,9 @@ L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel from one single-pass ncu capture of the bench command, keyed by (path, workload);
 # an entry is removed whenever that kernel changes.
-TRAFFIC = {}
+TRAFFIC = {
+    ("mma4", "large"): 419.24e6 + 7.11e6,   # scan_mma_kernel<e2m1>, 2048 x 16384
+}
 
 
 def env_int(name, default):

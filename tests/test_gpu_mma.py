@@ -132,3 +132,32 @@ def test_bounded_wait_times_out_and_context_survives(monkeypatch, name):
         tr, sc = h.scan(5)
     otr, osc, _ = oracle.scan_topk(g, ph, 5)
     assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("name", sorted(TENSOR))
+def test_tensor_exact_ties_and_copies(name):
+    # eight copies of one SNP and two of another: many triplets with exactly equal K2 at and
+    # around the k-th place, which the band, the pruning and the (K2, i, j, k) order must keep
+    d = gen.make_dataset(70, 900, 400, (0.2, 0.5), 1, seed=21, odds_ratio=6.0)
+    g = d.genotypes.copy()
+    for c in range(40, 48):
+        g[c] = g[3]
+    g[60] = g[61]
+    with epi.Handle(g, d.phenotype) as h:
+        h.set_option("path", name)
+        tr, sc = h.scan(64)
+    otr, osc, _ = oracle.scan_topk(g, d.phenotype, 64)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+def test_pruned_scan_with_a_crowded_band():
+    # no planted signal, narrow MAF range: the k-th best lies in the bulk of the K2
+    # distribution, so many tables fall inside the pruning bound and need the exact score
+    d = gen.make_dataset(90, 3000, 1500, (0.3, 0.35), 0, seed=23)
+    with epi.Handle(d.genotypes, d.phenotype) as h:
+        h.set_option("path", "mma4")
+        tr, sc = h.scan(512)
+        st = h.stats()
+    assert 0.0 < st["k2_prune_bound"] < 64.0
+    otr, osc, _ = oracle.scan_topk(d.genotypes, d.phenotype, 512)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
