@@ -606,60 +606,66 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             tc_st32(tmem + lane_off + kSfCol, one);
             tc_wait_st();
         }
-        StepCursor cc{};
-        cc.tl = 0;
-        cursor_load(cc, cds, tiles, my_tiles);
         // Software pipeline: step q's shared-memory loads are issued before the wait for step
-        // q-1's tensor-memory store, so the two latencies overlap.
+        // q-1's tensor-memory store, so the two latencies overlap.  Plain tile and step
+        // loops with ring counters keep the per-step bookkeeping to a few integer operations.
         int t_prev = -1;  // TMEM stage of a store issued but not yet published
         Ring rS{0, 0u}, rT{0, 0u};
         Ring rF{0, 0u};   // shared-memory stage of step q - kTm (released once its MMAs finish)
         int warm = 0;     // min(q, kTm)
-        for (; cc.valid; cursor_next(cc, cds, tiles, my_tiles)) {
-            const int s = rS.s, t = rT.s;
-            // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of step q
-            // have landed
-            const bool got =
-                mbar_wait_t(emptyT0 + 8 * t, rT.ph ^ 1u, abort_flag, prof ? &w_acc2 : nullptr) &&
-                mbar_wait_t(fullS0 + 8 * s, rS.ph, abort_flag, my_acc);
-            // tcgen05.st is warp-collective: the whole warp goes on or stops together
-            if (!__all_sync(0xffffffffu, got)) {
-                fail(cc.cd);
-                break;
-            }
-            tc_fence_after();
-            if (warm == kTm) {  // step q - kTm is complete: its K, Y, X stage goes back to the loader
-                if (warp == kProdWarp0 && lane == 0) mbar_arrive(emptyS0 + 8 * rF.s);
-                ring_next(rF, kSmStages);
-            } else {
-                ++warm;
-            }
-            const uint32_t xp = (2u * (uint32_t)(cc.tile.x & 63) + (uint32_t)ga) & 7u;
-            const uint8_t* ys = sY + s * kYChunk;
-            const uint8_t* xs = sX + s * kXBytes + ga * 128;
-            uint4 y[8], x[8];
+        bool ok = true;
+        for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+            const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
+            const CohortDev* cd = cds + tile.w;
+            const int nsteps = cd->KS[0] + cd->KS[1];
+            const uint32_t xp = (2u * (uint32_t)(tile.x & 63) + (uint32_t)ga) & 7u;
+            const uint8_t* xrow = sX + ga * 128;
+            for (int q = 0; q < nsteps; ++q) {
+                const int s = rS.s, t = rT.s;
+                // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of
+                // step q have landed
+                const bool got =
+                    mbar_wait_t(emptyT0 + 8 * t, rT.ph ^ 1u, abort_flag, prof ? &w_acc2 : nullptr) &&
+                    mbar_wait_t(fullS0 + 8 * s, rS.ph, abort_flag, my_acc);
+                // tcgen05.st is warp-collective: the whole warp goes on or stops together
+                if (!__all_sync(0xffffffffu, got)) {
+                    fail(cd);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (warm == kTm) {  // step q - kTm is complete: its stage goes back to the loader
+                    if (warp == kProdWarp0 && lane == 0) mbar_arrive(emptyS0 + 8 * rF.s);
+                    ring_next(rF, kSmStages);
+                } else {
+                    ++warm;
+                }
+                const uint8_t* ys = sY + s * kYChunk;
+                const uint8_t* xs = xrow + s * kXBytes;
+                uint4 y[8], x[8];
 #pragma unroll
-            for (uint32_t u = 0; u < 8; ++u) {
-                y[u] = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
-                x[u] = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
-            }
-            if (t_prev >= 0) {  // publish step q-1
-                tc_wait_st();
-                tc_fence_before();
-                mbar_arrive(fullT0 + 8 * t_prev);
-            }
-            uint32_t v[32];
+                for (uint32_t u = 0; u < 8; ++u) {
+                    y[u] = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
+                    x[u] = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
+                }
+                if (t_prev >= 0) {  // publish step q-1
+                    tc_wait_st();
+                    tc_fence_before();
+                    mbar_arrive(fullT0 + 8 * t_prev);
+                }
+                uint32_t v[32];
 #pragma unroll
-            for (uint32_t u = 0; u < 8; ++u) {
-                v[4 * u + 0] = y[u].x & x[u].x;
-                v[4 * u + 1] = y[u].y & x[u].y;
-                v[4 * u + 2] = y[u].z & x[u].z;
-                v[4 * u + 3] = y[u].w & x[u].w;
+                for (uint32_t u = 0; u < 8; ++u) {
+                    v[4 * u + 0] = y[u].x & x[u].x;
+                    v[4 * u + 1] = y[u].y & x[u].y;
+                    v[4 * u + 2] = y[u].z & x[u].z;
+                    v[4 * u + 3] = y[u].w & x[u].w;
+                }
+                tc_st32(tl_base + (uint32_t)t * kProdCols, v);
+                t_prev = t;
+                ring_next(rS, kSmStages);
+                ring_next(rT, kTm);
             }
-            tc_st32(tl_base + (uint32_t)t * kProdCols, v);
-            t_prev = t;
-            ring_next(rS, kSmStages);
-            ring_next(rT, kTm);
         }
         if (t_prev >= 0) {  // the last store (also on the abort path: nothing left in flight)
             tc_wait_st();
