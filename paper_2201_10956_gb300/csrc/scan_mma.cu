@@ -41,7 +41,7 @@ constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows
 constexpr int kThreads = 448;
 constexpr int kWarpMma = 1;
 constexpr int kEpiWarp0 = 2, kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
-constexpr int kProdWarp0 = 10, kProdWarps = 4, kProdThreads = kProdWarps * 32;
+constexpr int kProdWarp0 = 10, kProdWarps = 4;
 constexpr int kYChunk = kChunk / 2;      // one-hot rows (j, b) of 32 second SNPs: 64 rows
 constexpr int kXBytes = 256;             // one-hot rows (i, 0) and (i, 1): 2 rows
 constexpr int kTmemCols = 512;
@@ -57,6 +57,7 @@ static_assert(kRegions * 128 + 4 * kProdCols <= kTmemCols, "tensor memory budget
 static_assert(kRegions * 128 + 3 * kProdCols <= kSfCol, "tensor memory budget (E2M1)");
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
 constexpr int kCandCapMma = 1024;
+constexpr int kTRow = 80;                   // bytes per row of an epilogue transpose slab
 constexpr int kPruneAt = kCandCapMma / 2;   // local candidates that trigger a prune
 
 
@@ -447,6 +448,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNBars);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     EpiShared& es = *reinterpret_cast<EpiShared*>(reinterpret_cast<uint8_t*>(bars) + 256);
+    uint8_t* sT = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(&es) + sizeof(EpiShared) + 15) & ~static_cast<uintptr_t>(15));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t fullS0 = smem_u32(bars), emptyS0 = smem_u32(bars + kSmStages),
@@ -461,7 +464,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             mbar_init(emptyS0 + 8 * s, 1);
         }
         for (int s = 0; s < kTmStagesMax; ++s) {
-            mbar_init(fullT0 + 8 * s, kProdThreads);
+            mbar_init(fullT0 + 8 * s, kProdWarps);  // one arrival per producer warp
             mbar_init(emptyT0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) mbar_init(accF0 + 8 * b, 1);
@@ -648,10 +651,11 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     y[u] = *reinterpret_cast<const uint4*>(ys + sw128_off(yr, u));
                     x[u] = *reinterpret_cast<const uint4*>(xs + ((u ^ xp) << 4));
                 }
-                if (t_prev >= 0) {  // publish step q-1
+                if (t_prev >= 0) {  // publish step q-1: every lane's store is done, one arrival
                     tc_wait_st();
                     tc_fence_before();
-                    mbar_arrive(fullT0 + 8 * t_prev);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(fullT0 + 8 * t_prev);
                 }
                 uint32_t v[32];
 #pragma unroll
@@ -670,7 +674,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         if (t_prev >= 0) {  // the last store (also on the abort path: nothing left in flight)
             tc_wait_st();
             tc_fence_before();
-            mbar_arrive(fullT0 + 8 * t_prev);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(fullT0 + 8 * t_prev);
         }
     } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue (warps 2..9)
@@ -680,8 +685,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         const int tid = threadIdx.x - kEpiWarp0 * 32;   // 0..255
         const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;  // TMEM lane quadrant
         const int jj = 8 * quad + (lane >> 2), me = lane & 3;
-        const int h1 = me >> 1, l0 = me & 1;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        uint8_t* tw = sT + (warp - kEpiWarp0) * (32 * kTRow);  // this warp's transpose slab
         int cur = -1;
         Ring rR{0, 0u};
         for (long long tl = 0; tl < my_tiles; ++tl) {
@@ -750,33 +755,24 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
 #pragma unroll
                     for (int t = 0; t < 16; ++t) x[t] = has ? __float2int_rn(__uint_as_float(v[c][t])) : 0;
                     // x[4 blk + e]: column 16 g + 4 blk + e; lane `me` needs block `me` of all
-                    // four lanes.  Butterfly over lane bit 1, then bit 0.
-                    int ys[2][4], yp[2][4];
+                    // four lanes of its jj.  Through this warp's shared-memory slab: row = lane,
+                    // 16-byte unit = block (rows 80 bytes apart, so neither the stores nor the
+                    // loads below conflict); row 4 jjl + src then holds cells (a, b) = src.
+                    __syncwarp();  // the previous class's loads are done
 #pragma unroll
-                    for (int b0 = 0; b0 < 2; ++b0)
+                    for (int blk = 0; blk < 4; ++blk)
+                        *reinterpret_cast<int4*>(tw + lane * kTRow + blk * 16) =
+                            make_int4(x[4 * blk], x[4 * blk + 1], x[4 * blk + 2], x[4 * blk + 3]);
+                    __syncwarp();
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int lo = x[4 * b0 + e], hi = x[4 * (2 + b0) + e];
-                            ys[b0][e] = h1 ? hi : lo;
-                            yp[b0][e] = __shfl_xor_sync(0xffffffffu, h1 ? lo : hi, 2);
-                        }
-                    int w[4][4];  // w[d][e]: block `me` of lane me ^ d
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        w[0][e] = l0 ? ys[1][e] : ys[0][e];
-                        w[2][e] = l0 ? yp[1][e] : yp[0][e];
-                        w[1][e] = __shfl_xor_sync(0xffffffffu, l0 ? ys[0][e] : ys[1][e], 1);
-                        w[3][e] = __shfl_xor_sync(0xffffffffu, l0 ? yp[0][e] : yp[1][e], 1);
+                    for (int src = 0; src < 4; ++src) {
+                        const int4 q = *reinterpret_cast<const int4*>(
+                            tw + (4 * (lane >> 2) + src) * kTRow + me * 16);
+                        n8[c][0][2 * src] = q.x;      // (m = 0, z = 0)
+                        n8[c][0][2 * src + 1] = q.y;  // (m = 0, z = 1)
+                        n8[c][1][2 * src] = q.z;      // (m = 1, z = 0)
+                        n8[c][1][2 * src + 1] = q.w;  // (m = 1, z = 1)
                     }
-                    // lane me ^ d holds cells (a, b) = me ^ d; place by (a, b)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int t0 = l0 ? w[p ^ 1][e] : w[p][e];
-                            const int t1 = l0 ? w[p ^ 3][e] : w[p ^ 2][e];
-                            n8[c][e >> 1][2 * p + (e & 1)] = h1 ? t1 : t0;
-                        }
                 }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
@@ -885,7 +881,8 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
 }  // namespace
 
 size_t scan_mma_smem() {
-    return 1024 + kSmStages * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 64;
+    return 1024 + kSmStages * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 16 +
+           kEpiWarps * 32 * kTRow + 64;
 }
 
 int mma_samples_per_step(int kind) {
