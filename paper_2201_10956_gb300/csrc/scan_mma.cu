@@ -420,7 +420,7 @@ __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds
     cursor_load(cu, cds, tiles, my_tiles);
 }
 
-template <int kKind>
+template <int kKind, bool kProf>
 __global__ void __launch_bounds__(kThreads, 1)
 scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
                 unsigned long long* __restrict__ prof) {
@@ -429,9 +429,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     //   regions, [3] producers (lane 0 of each producer warp) on full stages, [4] epilogue
     //   (lane 0 of each epilogue warp) on full accumulators, [5] kernel cycles of this CTA,
     //   [6] producers on free tensor-memory stages, [7] MMA issuer issuing MMAs and commits
-    const long long t_start = clock64();
+    const long long t_start = kProf ? clock64() : 0;
     unsigned long long w_acc = 0, busy = 0, w_acc2 = 0;
-    unsigned long long* my_acc = prof ? &w_acc : nullptr;
+    unsigned long long* my_acc = kProf ? &w_acc : nullptr;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned stage buffers (the 128B swizzle pattern is anchored there)
     uint8_t* base = reinterpret_cast<uint8_t*>(
@@ -541,15 +541,20 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 if (!mbar_wait(drain0, 0, abort_flag)) fail(cds);
                 ok = false;
             }
-            Ring rS{0, 0u}, rT{0, 0u}, rR{0, 0u};
+            // The issuing thread's own instruction latency bounds the step rate, so the loop
+            // keeps its stage addresses and phases as incrementally updated registers.
+            Ring rR{0, 0u};
             const uint64_t db0 = sw128_desc(smem_u32(sK));
+            uint64_t db = db0;                        // B descriptor of shared-memory stage s
+            int s = 0, t = 0;                         // shared-memory / TMEM stage
+            uint32_t phT = 0, fT = fullT0, eT = emptyT0, ta = tmem + kProdCol0;
             for (long long tl = 0; tl < my_tiles && ok; ++tl) {
                 const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
                 const CohortDev* cd = cds + tile.w;
                 const int KS[2] = {cd->KS[0], cd->KS[1]};
                 for (int c = 0; c < 2 && ok; ++c) {
                     // accumulator region of segment (tile, class): a ring of kRegions
-                    if (!mbar_wait_t(regE0 + 8 * rR.s, rR.ph ^ 1u, abort_flag, prof ? &busy : nullptr)) {
+                    if (!mbar_wait_t(regE0 + 8 * rR.s, rR.ph ^ 1u, abort_flag, kProf ? &busy : nullptr)) {
                         fail(cd);
                         ok = false;
                         break;
@@ -560,26 +565,40 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     for (int ks = 0; ks < KS[c]; ++ks) {
                         // the producers arrive on fullT only after they saw the step's bulk
                         // copies land (fullS), so one wait covers both operands
-                        if (!mbar_wait_t(fullT0 + 8 * rT.s, rT.ph, abort_flag, my_acc)) {
+                        if (!mbar_wait_t(fT, phT, abort_flag, my_acc)) {
                             fail(cd);
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const long long t_issue = prof ? clock64() : 0;
-                        const uint32_t ta = tmem + kProdCol0 + (uint32_t)rT.s * kProdCols;
-                        const uint64_t db = db0 + (uint64_t)((rS.s * kChunk) >> 4);
+                        const long long t_issue = kProf ? clock64() : 0;
+                        tc_mma_ts<kKind>(d, ta, db, idesc_of<kKind>(), ks > 0 ? 1u : 0u,
+                                         tmem + kSfCol, tmem + kSfCol + 16);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
-                            tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(),
-                                             (ks > 0 || kk > 0) ? 1u : 0u, tmem + kSfCol,
-                                             tmem + kSfCol + 16);
+                        for (int kk = 1; kk < 4; ++kk)  // 32 bytes of K per instruction
+                            tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(), 1u,
+                                             tmem + kSfCol, tmem + kSfCol + 16);
                         // one commit per step: its arrival frees the TMEM A stage, and the
                         // producers then release the shared-memory stage to the loader
-                        tc_commit(emptyT0 + 8 * rT.s);
-                        if (prof) w_acc2 += (unsigned long long)(clock64() - t_issue);
-                        ring_next(rS, kSmStages);
-                        ring_next(rT, kTm);
+                        tc_commit(eT);
+                        if (kProf) w_acc2 += (unsigned long long)(clock64() - t_issue);
+                        if (++t == kTm) {
+                            t = 0;
+                            phT ^= 1u;
+                            fT = fullT0;
+                            eT = emptyT0;
+                            ta = tmem + kProdCol0;
+                        } else {
+                            fT += 8;
+                            eT += 8;
+                            ta += kProdCols;
+                        }
+                        if (++s == kSmStages) {
+                            s = 0;
+                            db = db0;
+                        } else {
+                            db += (uint64_t)(kChunk >> 4);
+                        }
                     }
                 }
                 if (ok) tc_commit(accF0 + 8 * (int)(tl & 1));
@@ -628,7 +647,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of
                 // step q have landed
                 const bool got =
-                    mbar_wait_t(emptyT0 + 8 * t, rT.ph ^ 1u, abort_flag, prof ? &w_acc2 : nullptr) &&
+                    mbar_wait_t(emptyT0 + 8 * t, rT.ph ^ 1u, abort_flag, kProf ? &w_acc2 : nullptr) &&
                     mbar_wait_t(fullS0 + 8 * s, rS.ph, abort_flag, my_acc);
                 // tcgen05.st is warp-collective: the whole warp goes on or stops together
                 if (!__all_sync(0xffffffffu, got)) {
@@ -826,7 +845,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         epi_bar();
         if (cur >= 0) epi_prune(cds[cur], es, min(es.cnt, kCandCapMma), tid, true);
     }
-    if (prof) {
+    if (kProf) {
         const unsigned long long total = (unsigned long long)(clock64() - t_start);
         if (warp == 0 && lane == 0) atomicAdd(prof + 0, w_acc);
         if (warp == kWarpMma && lane == 0) {
@@ -903,15 +922,24 @@ cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0
     return cudaGetLastError();
 }
 
+template <int kKind, bool kProf>
+static cudaError_t launch_variant(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
+                                  int grid, cudaStream_t st, unsigned long long* prof) {
+    const size_t smem = scan_mma_smem();
+    const cudaError_t e = cudaFuncSetAttribute(
+        scan_mma_kernel<kKind, kProf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    scan_mma_kernel<kKind, kProf><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
+    return cudaGetLastError();
+}
+
+// Role profiling (option "profile") is a separate instantiation, so the normal kernel's hot
+// loops carry no clock reads or profiling branches.
 template <int kKind>
 static cudaError_t launch_kind(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                                int grid, cudaStream_t st, unsigned long long* prof) {
-    const size_t smem = scan_mma_smem();
-    const cudaError_t e = cudaFuncSetAttribute(
-        scan_mma_kernel<kKind>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    scan_mma_kernel<kKind><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
-    return cudaGetLastError();
+    return prof ? launch_variant<kKind, true>(cohorts, tiles, n_tiles, grid, st, prof)
+                : launch_variant<kKind, false>(cohorts, tiles, n_tiles, grid, st, prof);
 }
 
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
