@@ -761,6 +761,24 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 // the global band threshold only shrinks: a copy read once per group is a
                 // valid (looser) filter
                 const float thr_g = __uint_as_float(*(volatile unsigned*)&ctrl->thr);
+                // this lane's two triplets (k = kb0 + 8 g + 2 me + m): their pair-table rows
+                // are requested first, so the loads overlap the TMEM read and the transpose
+                // (an index outside the triangle reads entry 0 and is not used)
+                int4 tik[2][2], tjk[2][2];
+                int2 tmk[2][2];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int k = kb0 + 8 * g + 2 * me + m;
+                    const bool val = jrow && k > j && k < M;
+                    const long long pik = val ? pair_index(i, k) : 0, pjk = val ? pair_index(j, k) : 0;
+                    const int kq = val ? k : 0;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        tik[m][c] = __ldg(pt.pt + c * pt.n_pairs + pik);
+                        tjk[m][c] = __ldg(pt.pt + c * pt.n_pairs + pjk);
+                        tmk[m][c] = __ldg(pt.marg + (size_t)c * M + kq);
+                    }
+                }
                 uint32_t v[2][16];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) tc_ld16(tmem + lane_base + rc[c] + 16 * g, v[c]);
@@ -797,13 +815,11 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 for (int m = 0; m < 2; ++m) {
                     const int k = kb0 + 8 * g + 2 * me + m;
                     if (!(jrow && k > j && k < M)) continue;
-                    const long long pik = pair_index(i, k), pjk = pair_index(j, k);
                     int r0[kCells], r1[kCells];
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
-                        derive27(n8[c][m], pxy[c], __ldg(pt.pt + c * pt.n_pairs + pik),
-                                 __ldg(pt.pt + c * pt.n_pairs + pjk), mx[c], my[c],
-                                 __ldg(pt.marg + (size_t)c * M + k), pt.n_c[c], c ? r1 : r0);
+                        derive27(n8[c][m], pxy[c], tik[m][c], tjk[m][c], mx[c], my[c], tmk[m][c],
+                                 pt.n_c[c], c ? r1 : r0);
                     // guard the log-factorial lookups: derive27 makes every class sum N_c, so
                     // no negative cell means every cell lies in [0, N_c]
                     int neg = 0;
