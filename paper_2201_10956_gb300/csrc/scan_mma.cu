@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kKB = 64;                  // third SNPs per tile (B rows = 2 per SNP)
 constexpr int kJB = 32;                  // second SNPs per tile (A rows = 4 per SNP)
-constexpr int kSmStages = 6;             // shared-memory ring: K, Y, X chunks of one step
+constexpr int kSmStages = 5;             // shared-memory ring: K, Y, X chunks of one step
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
 // 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps
 // per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM lane).

@@ -161,3 +161,19 @@ def test_pruned_scan_with_a_crowded_band():
     assert 0.0 < st["k2_prune_bound"] < 64.0
     otr, osc, _ = oracle.scan_topk(d.genotypes, d.phenotype, 512)
     assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("name", sorted(TENSOR))
+def test_tensor_scan_full_size_matches_popc8(name):
+    # the 2048 x 16384 workload: every tensor kind's top-10 equals the 8-cell POPC scan's
+    # (itself checked against the oracle) and the oracle's FP64 scores of those triplets
+    d = gen.make_config("large")
+    g, ph = d.genotypes, d.phenotype
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", "popc8")
+        ref_t, ref_s = h.scan(10)
+        h.set_option("path", name)
+        tr, sc = h.scan(10)
+    assert np.array_equal(tr, ref_t) and np.array_equal(sc, ref_s)
+    assert np.array_equal(oracle.scores(g, ph, tr), sc)
+    assert tuple(tr[0]) in [tuple(p) for p in d.planted]
