@@ -115,7 +115,7 @@ cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long
                                cudaStream_t st);
 cudaError_t launch_scan_popc8(const ScanArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 size_t scan_popc8_smem(const Planes& pl);
-size_t scan_mma_smem();
+size_t scan_mma_smem(int kind);
 // Element kinds of the tensor-core scan's 0/1 operands: FP16, FP8 E4M3, block-scaled FP4 E2M1
 // (two per byte).  A 128-byte operand row holds 64, 128 or 256 samples.
 enum { kKindF16 = 0, kKindE4M3 = 1, kKindE2M1 = 2 };

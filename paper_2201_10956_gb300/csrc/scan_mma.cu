@@ -34,7 +34,9 @@ namespace {
 
 constexpr int kKB = 64;                  // third SNPs per tile (B rows = 2 per SNP)
 constexpr int kJB = 32;                  // second SNPs per tile (A rows = 4 per SNP)
-constexpr int kSmStages = 5;             // shared-memory ring: K, Y, X chunks of one step
+// shared-memory ring (K, Y, X chunks of one step): sm_stages<kind>() = TMEM A stages + 2, since
+// a stage goes back to the loader only once its step's MMAs (kTm steps earlier) are complete
+constexpr int kSmStagesMax = 6;
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
 // 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps
 // per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM lane).
@@ -53,6 +55,9 @@ constexpr int kTmStagesMax = 4;
 // tensor-memory ring of A stages: four, or three beside the block-scale columns
 template <int kKind>
 __host__ __device__ constexpr int tm_stages() { return kKind == kKindE2M1 ? 3 : 4; }
+template <int kKind>
+__host__ __device__ constexpr int sm_stages() { return tm_stages<kKind>() + 2; }
+static_assert(4 + 2 <= kSmStagesMax, "shared-memory ring");
 static_assert(kRegions * 128 + 4 * kProdCols <= kTmemCols, "tensor memory budget");
 static_assert(kRegions * 128 + 3 * kProdCols <= kSfCol, "tensor memory budget (E2M1)");
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no legitimate wait is close
@@ -437,6 +442,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
     uint8_t* base = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     constexpr int kTm = tm_stages<kKind>();
+    constexpr int kSmStages = sm_stages<kKind>();
     uint8_t* sK = base;                                    // [kSmStages][16 KB] third-SNP rows
     uint8_t* sY = base + kSmStages * kChunk;               // [kSmStages][8 KB]
     uint8_t* sX = sY + kSmStages * kYChunk;                // [kSmStages][256 B]
@@ -915,8 +921,9 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
 
 }  // namespace
 
-size_t scan_mma_smem() {
-    return 1024 + kSmStages * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 16 +
+size_t scan_mma_smem(int kind) {
+    const int sm = kind == kKindE2M1 ? sm_stages<kKindE2M1>() : sm_stages<kKindE4M3>();
+    return 1024 + sm * (kChunk + kYChunk + kXBytes) + 256 + sizeof(EpiShared) + 16 +
            kEpiWarps * 32 * kTRow + 64;
 }
 
@@ -941,7 +948,7 @@ cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0
 template <int kKind, bool kProf>
 static cudaError_t launch_variant(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                                   int grid, cudaStream_t st, unsigned long long* prof) {
-    const size_t smem = scan_mma_smem();
+    const size_t smem = scan_mma_smem(kKind);
     const cudaError_t e = cudaFuncSetAttribute(
         scan_mma_kernel<kKind, kProf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
