@@ -55,6 +55,9 @@ class Oracle:
                                       ctypes.c_int32]
         lib.oracle_scan_topk.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P, P,
                                          ctypes.c_int32]
+        lib.oracle_pair_tables.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, P, P]
+        lib.oracle_scan_pairs_topk.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                               P, P, ctypes.c_int32]
         for f in (lib.oracle_log_factorials, lib.oracle_tables, lib.oracle_k2, lib.oracle_scores,
                   lib.oracle_scan_topk):
             f.restype = ctypes.c_int
@@ -107,6 +110,28 @@ class Oracle:
         return trip, sc, rc
 
 
+    def pair_tables(self, genotypes, phenotype, pairs) -> np.ndarray:
+        """[n, 2, 9] int32 tables of the given SNP pairs (cell = 3 gX + gY)."""
+        g, p = _inputs(genotypes, phenotype)
+        t = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        out = np.empty((t.shape[0], 2, 9), dtype=np.int32)
+        if self._lib.oracle_pair_tables(_ptr(g), _ptr(p), g.shape[0], g.shape[1], t.shape[0],
+                                        _ptr(t), _ptr(out)):
+            raise ValueError("bad pair index or genotype/phenotype value")
+        return out
+
+    def scan_pairs_topk(self, genotypes, phenotype, top_k: int, threads: int = 0):
+        """Exhaustive pairwise scan; returns (pairs int32 [k, 2], K2 float64 [k], threads used)."""
+        g, p = _inputs(genotypes, phenotype)
+        pairs = np.empty((top_k, 2), dtype=np.int32)
+        sc = np.empty(top_k, dtype=np.float64)
+        rc = self._lib.oracle_scan_pairs_topk(_ptr(g), _ptr(p), g.shape[0], g.shape[1], top_k,
+                                              _ptr(pairs), _ptr(sc), threads)
+        if rc < 0:
+            raise ValueError("bad arguments or values")
+        return pairs, sc, rc
+
+
 _default = None
 
 
@@ -135,3 +160,11 @@ def scores(genotypes, phenotype, triplets, threads: int = 0):
 
 def scan_topk(genotypes, phenotype, top_k, threads: int = 0):
     return default().scan_topk(genotypes, phenotype, top_k, threads)
+
+
+def pair_tables(genotypes, phenotype, pairs):
+    return default().pair_tables(genotypes, phenotype, pairs)
+
+
+def scan_pairs_topk(genotypes, phenotype, top_k, threads: int = 0):
+    return default().scan_pairs_topk(genotypes, phenotype, top_k, threads)

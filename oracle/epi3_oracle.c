@@ -25,9 +25,14 @@
  *   - Sec. III: the solution is the triplet of lowest K2.  Generalised to the
  *     k best under the total order (K2 ascending, then i, j, k ascending).
  *
+ *   - Eq. 1 is stated for any number of interacting SNPs; for two SNPs
+ *     (x, y) the table has 3^2 = 9 cells per class, cell = 3 * gX + gY, and
+ *     the same K2 in cell order 0..8 (the pairwise, second-order scan).
+ *
  * Pins (tests/test_oracle_pins.py): brute-force numpy counting, table
  * invariants, exact K2 from big-integer factorials, hand-worked values,
- * symmetries, degenerate inputs and planted-triplet recovery.
+ * symmetries, degenerate inputs and planted-triplet recovery; the pairwise
+ * functions also against the triplet functions on a monomorphic third SNP.
  */
 #include <math.h>
 #include <stdint.h>
@@ -218,6 +223,105 @@ int oracle_scan_topk(const uint8_t* geno, const uint8_t* pheno, int32_t n_snps,
         out_trip[3 * r] = lists[r].i;
         out_trip[3 * r + 1] = lists[r].j;
         out_trip[3 * r + 2] = lists[r].k;
+        out_k2[r] = lists[r].k2;
+    }
+    free(lists);
+    free(lens);
+    free(lf);
+    return bad ? -1 : nt;
+}
+
+/* ---------------------------------------------------------------- pairs */
+#define NPCELL 9
+
+/* Frequency table of SNPs (x, y); ft[c * 9 + 3 * gX + gY]. */
+static int count_pair(const uint8_t* geno, const uint8_t* pheno, int64_t n_samples, int64_t x,
+                      int64_t y, int32_t* ft) {
+    memset(ft, 0, sizeof(int32_t) * 2 * NPCELL);
+    const uint8_t* gx = geno + x * n_samples;
+    const uint8_t* gy = geno + y * n_samples;
+    for (int64_t s = 0; s < n_samples; ++s) {
+        int c = pheno[s];
+        int a = gx[s], b = gy[s];
+        if (c > 1 || a > 2 || b > 2) return -1;
+        ft[c * NPCELL + 3 * a + b] += 1;
+    }
+    return 0;
+}
+
+/* K2 of one 2 x 9 table, cell order 0..8, as k2_of_table. */
+static double k2_of_pair(const int32_t* ft, const double* lf) {
+    double k2 = 0.0;
+    for (int cell = 0; cell < NPCELL; ++cell) {
+        int32_t r0 = ft[cell], r1 = ft[NPCELL + cell];
+        double term = (lf[r0 + r1 + 1] - lf[r0]) - lf[r1];
+        k2 = k2 + term;
+    }
+    return k2;
+}
+
+/* Tables of n pairs (two distinct SNP indices, in the given order): out [n][2][9]. */
+int oracle_pair_tables(const uint8_t* geno, const uint8_t* pheno, int32_t n_snps,
+                       int64_t n_samples, int64_t n, const int32_t* pairs, int32_t* out) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+    for (int64_t t = 0; t < n; ++t) {
+        int32_t x = pairs[2 * t], y = pairs[2 * t + 1];
+        if (x < 0 || y < 0 || x >= n_snps || y >= n_snps) {
+            bad = 1;
+            continue;
+        }
+        if (count_pair(geno, pheno, n_samples, x, y, out + t * 2 * NPCELL)) bad = 1;
+    }
+    return bad ? -1 : 0;
+}
+
+/* Exhaustive pairwise scan over every i < j: the top_k pairs by (K2, i, j).
+ * out_pairs [top_k][2], out_k2 [top_k].  Returns threads used (> 0) or a negative error. */
+int oracle_scan_pairs_topk(const uint8_t* geno, const uint8_t* pheno, int32_t n_snps,
+                           int64_t n_samples, int32_t top_k, int32_t* out_pairs, double* out_k2,
+                           int32_t n_threads) {
+    int64_t m = n_snps;
+    if (m < 2 || top_k < 1 || top_k > m * (m - 1) / 2) return -1;
+    double* lf = (double*)malloc(sizeof(double) * (size_t)(n_samples + 2));
+    if (!lf) return -2;
+    oracle_log_factorials((int32_t)(n_samples + 1), lf);
+    int nt = 1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+    nt = omp_get_max_threads();
+#endif
+    entry* lists = (entry*)malloc(sizeof(entry) * (size_t)top_k * nt);
+    int32_t* lens = (int32_t*)calloc((size_t)nt, sizeof(int32_t));
+    int bad = 0;
+#pragma omp parallel reduction(| : bad)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        entry* mine = lists + (size_t)tid * top_k;
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t i = 0; i < n_snps; ++i)
+            for (int32_t j = i + 1; j < n_snps; ++j) {
+                int32_t ft[2 * NPCELL];
+                if (count_pair(geno, pheno, n_samples, i, j, ft)) {
+                    bad = 1;
+                    continue;
+                }
+                entry e = {k2_of_pair(ft, lf), i, j, 0};
+                keep_best(mine, &lens[tid], top_k, &e);
+            }
+    }
+    int32_t total = 0;
+    for (int t = 0; t < nt; ++t) {
+        memmove(lists + total, lists + (size_t)t * top_k, sizeof(entry) * lens[t]);
+        total += lens[t];
+    }
+    qsort(lists, (size_t)total, sizeof(entry), cmp_entry);
+    for (int32_t r = 0; r < top_k && r < total; ++r) {
+        out_pairs[2 * r] = lists[r].i;
+        out_pairs[2 * r + 1] = lists[r].j;
         out_k2[r] = lists[r].k2;
     }
     free(lists);

@@ -12,7 +12,9 @@ oracle's own code path as its expected value:
 * log-factorials: math.lgamma;
 * ranking: numpy lexsort over every triplet, exact FP64 ties from duplicated
   SNP columns, and recovery of a strongly planted triplet (lowest K2 wins,
-  Sec. III).
+  Sec. III);
+* pairs (Eq. 1 for two SNPs, 9 cells): numpy bincount, big-integer K2, and the
+  triplet K2 of a monomorphic third SNP, which must equal the pair K2 exactly.
 """
 from __future__ import annotations
 
@@ -215,6 +217,80 @@ def check_planted_recovery(o):
         assert tuple(tr[0]) == d.planted[0], (seed, tr[0], d.planted[0])
 
 
+# ---------------------------------------------------------------- pairs (Eq. 1, two SNPs)
+def all_pairs(m):
+    return np.array(list(itertools.combinations(range(m), 2)), dtype=np.int32).reshape(-1, 2)
+
+
+def numpy_pair_tables(g, ph, pairs):
+    """Independent counting: bincount of class*9 + 3 gX + gY."""
+    out = np.empty((len(pairs), 2, 9), dtype=np.int64)
+    for t, (x, y) in enumerate(pairs):
+        idx = ph.astype(np.int64) * 9 + 3 * g[x].astype(np.int64) + g[y]
+        out[t] = np.bincount(idx, minlength=18).reshape(2, 9)
+    return out
+
+
+def exact_pair_k2(table):
+    num = 1
+    for c in range(9):
+        r0, r1 = int(table[0][c]), int(table[1][c])
+        num *= math.factorial(r0 + r1 + 1) // (math.factorial(r0) * math.factorial(r1))
+    return math.log(num)
+
+
+def check_pair_tables_bruteforce(o):
+    for (m, n, n1, seed) in [(7, 53, 20, 41), (5, 130, 129, 42)]:
+        g, ph = tiny_data(m, n, n1, seed)
+        pairs = all_pairs(m)
+        assert np.array_equal(o.pair_tables(g, ph, pairs), numpy_pair_tables(g, ph, pairs))
+        rev = pairs[:, ::-1]                                # order matters: cell = 3 gX + gY
+        assert np.array_equal(o.pair_tables(g, ph, rev), numpy_pair_tables(g, ph, rev))
+
+
+def check_pair_scan_bruteforce(o):
+    for (m, n, n1, seed, k) in [(12, 90, 40, 43, 9), (9, 33, 11, 44, 36), (20, 257, 128, 45, 50)]:
+        g, ph = tiny_data(m, n, n1, seed)
+        pairs = all_pairs(m)
+        s = np.array([exact_pair_k2(t) for t in numpy_pair_tables(g, ph, pairs)])
+        tr, sc, _ = o.scan_pairs_topk(g, ph, k)
+        assert np.allclose(sc, np.sort(s)[:k], rtol=1e-13)
+        # order: K2 ascending, then (i, j); the oracle's own FP64 values decide exact ties
+        full_t, full_s, _ = o.scan_pairs_topk(g, ph, len(pairs))
+        order = np.lexsort((full_t[:, 1], full_t[:, 0], full_s))
+        assert np.array_equal(order, np.arange(len(pairs)))
+        assert np.array_equal(tr, full_t[:k]) and np.array_equal(sc, full_s[:k])
+        assert {tuple(p) for p in full_t} == {tuple(p) for p in pairs}
+
+
+def check_pair_vs_triplet(o, seed=46):
+    # a monomorphic third SNP reduces a triplet's 27-cell table to the pair's 9 cells (the
+    # other 18 are empty and add exactly 0.0), so its K2 is the pair's, bit for bit
+    g, ph = tiny_data(8, 150, 70, seed)
+    g[7] = 0
+    pt, ps, _ = o.scan_pairs_topk(g[:7], ph, 21)
+    trip = np.concatenate([pt, np.full((len(pt), 1), 7, dtype=np.int32)], axis=1)
+    assert np.array_equal(o.scores(g, ph, trip), ps)
+
+
+def check_pair_ties_and_degenerate(o):
+    g, ph = tiny_data(10, 200, 90, 47)
+    g[8] = g[2]          # pairs (2, x), (8, x) with x on the same side of both: equal tables
+    tr, sc, _ = o.scan_pairs_topk(g, ph, 45)
+    pos = {tuple(p): r for r, p in enumerate(tr)}
+    for x in (0, 1, 9):
+        a, b = tuple(sorted((2, x))), tuple(sorted((8, x)))
+        assert a in pos and b in pos          # 45 = every pair of 10 SNPs
+        assert sc[pos[a]] == sc[pos[b]]
+        assert (pos[a] < pos[b]) == (a < b)
+    g2, ph2 = tiny_data(2, 40, 15, 48)                    # M = 2: the only pair
+    tr, sc, _ = o.scan_pairs_topk(g2, ph2, 1)
+    assert tr.tolist() == [[0, 1]]
+    assert math.isclose(sc[0], exact_pair_k2(numpy_pair_tables(g2, ph2, [[0, 1]])[0]), rel_tol=1e-13)
+
+
 ALL_CHECKS = [check_lf, check_hand_values, check_k2_bigint, check_tables_bruteforce,
               check_invariants, check_symmetries, check_monomorphic, check_degenerate,
-              check_scan_bruteforce, check_ties, check_planted_recovery]
+              check_scan_bruteforce, check_ties, check_planted_recovery,
+              check_pair_tables_bruteforce, check_pair_scan_bruteforce, check_pair_vs_triplet,
+              check_pair_ties_and_degenerate]

@@ -229,12 +229,36 @@ def test_medium_config_sampled(path):
 
 
 @pytest.mark.slow
-def test_large_config_sampled():
+@pytest.mark.parametrize("path", ["popc8", "auto"])
+def test_large_config_sampled(path):
     d = gen.make_config("large")
-    sampled_parity(d, 100_000, 10, seed=1)
+    sampled_parity(d, 100_000, 10, seed=1, path=path)
+
+
+def triplets_with(m, p):
+    """Every triplet i<j<k of m SNPs that contains SNP p."""
+    rest = np.array([x for x in range(m) if x != p], dtype=np.int32)
+    a, b = np.triu_indices(m - 1, 1)
+    t = np.stack([rest[a], rest[b], np.full(a.size, p, dtype=np.int32)], axis=1)
+    return np.sort(t, axis=1).astype(np.int32)
 
 
 @pytest.mark.slow
-def test_stress_config_sampled():
+@pytest.mark.parametrize("path", ["popc8", "auto"])
+def test_stress_config_sampled(path):
     d = gen.make_config("stress")
-    sampled_parity(d, 200_000, 64, seed=2)
+    sampled_parity(d, 200_000, 64, seed=2, path=path)
+    # every triplet containing one SNP of each planted triplet (4 x C(4095, 2) = 3.4e7): none
+    # outside the answer scores below its 64th (FP64 scores of the per-triplet table kernel,
+    # a code path separate from the scans)
+    g, ph = d.genotypes, d.phenotype
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", path)
+        tr, sc = h.scan(64)
+        got = {tuple(t) for t in tr}
+        for p in sorted({t[0] for t in d.planted}):
+            trip = triplets_with(d.n_snps, p)
+            _, s64 = h.scores(trip)
+            for t in trip[s64 < sc[-1]]:
+                assert tuple(t) in got
+            assert not np.any(s64 < sc[0])

@@ -18,6 +18,12 @@ MUTANTS = {
     "tiebreak_reversed": ("return a->i < b->i;", "return a->i > b->i;"),
     "last_sample_dropped": ("s < n_samples; ++s", "s + 1 < n_samples; ++s"),
     "k_loop_skips": ("int32_t k = j + 1;", "int32_t k = j + 2;"),
+    "pair_cell_transposed": ("ft[c * NPCELL + 3 * a + b]", "ft[c * NPCELL + a + 3 * b]"),
+    "pair_classes_swapped": ("ft[c * NPCELL + 3 * a + b] += 1;",
+                             "ft[(1 - c) * NPCELL + 3 * a + b] += 1;"),
+    "pair_last_cell_skipped": ("cell < NPCELL; ++cell", "cell < NPCELL - 1; ++cell"),
+    "pair_j_loop_skips": ("for (int32_t j = i + 1; j < n_snps; ++j) {\n                int32_t ft[2 * NPCELL];",
+                          "for (int32_t j = i + 2; j < n_snps; ++j) {\n                int32_t ft[2 * NPCELL];"),
 }
 
 
