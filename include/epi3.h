@@ -114,6 +114,19 @@ int epi3_scan(epi3_handle* h, int32_t top_k, int32_t* out_triplets, double* out_
 int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_t top_k,
                     int32_t* out_triplets, double* out_scores, int32_t* n_out);
 
+/*
+ * Pairwise (second-order) scan: Eq. 1 applied to two SNPs (3^2 cells x {control, case},
+ * cell = 3 gX + gY; the paper states the score for any number of interacting SNPs).  Every
+ * pair i < j is scored in FP64 from its exact table, summed in cell order 0..8 with the same
+ * log-factorial table as the triplet rescoring; the top_k pairs by (K2 ascending, then i, j)
+ * are returned.
+ *   top_k        1..min(EPI3_MAX_TOPK, C(M,2)).
+ *   out_pairs    [top_k][2] int32, i < j, 0-based;  out_scores [top_k] FP64 K2, ascending.
+ * Outputs are host memory unless the handle was created with EPI3_DEVICE_PTRS.  Returns
+ * EPI3_OK, EPI3_ERR_ARG (bad top_k or null pointers), EPI3_ERR_OOM or EPI3_ERR_CUDA.
+ */
+int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* out_scores);
+
 /* Release the handle's device memory, stream (if owned) and events. */
 int epi3_destroy(epi3_handle* h);
 

@@ -90,6 +90,8 @@ struct epi3_handle {
     double* d_out_scores = nullptr;
     int* d_out_trip = nullptr;
     int4* d_pt = nullptr;         // pair tables (8-cell forms), built on first use
+    void* d_pair_scratch = nullptr;  // pairwise scan: selection passes + outputs
+    size_t pair_scratch_bytes = 0;
     int2* d_marg = nullptr;
     PairTables ptab{};
     uint8_t* d_oh = nullptr;      // pre-tiled one-hot operand of the tensor-core form
@@ -127,6 +129,7 @@ void release(epi3_handle* h) {
     cudaFree(h->d_out_scores);
     cudaFree(h->d_out_trip);
     cudaFree(h->d_pt);
+    cudaFree(h->d_pair_scratch);
     cudaFree(h->d_marg);
     cudaFree(h->d_oh);
     cudaFree(h->d_tiles);
@@ -768,6 +771,49 @@ int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_
     g_err.clear();
     (void)cudaGetLastError();  // do not report an earlier call's error as ours
     return scan_impl(h, pair_begin, pair_end, top_k, out_triplets, out_scores, n_out, false);
+}
+
+int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* out_scores) {
+    g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
+    if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    if (!out_pairs || !out_scores) return fail(EPI3_ERR_ARG, "null output pointer");
+    const long long np = pairs(h->M);
+    if (top_k < 1 || top_k > EPI3_MAX_TOPK || top_k > np)
+        return fail(EPI3_ERR_ARG, "top_k %d outside 1..min(%d, %lld)", top_k, EPI3_MAX_TOPK, np);
+    int rc = ensure_pair_tables(h);
+    if (rc != EPI3_OK) return rc;
+    const size_t sel = (pair_scan_scratch(np, top_k) + 255) & ~(size_t)255;
+    const size_t need = sel + sizeof(double) * (size_t)top_k + sizeof(int32_t) * 2 * (size_t)top_k;
+    if (h->pair_scratch_bytes < need) {
+        cudaFree(h->d_pair_scratch);
+        h->d_pair_scratch = nullptr;
+        h->pair_scratch_bytes = 0;
+        CK(dev_alloc(&h->d_pair_scratch, need), "alloc pair-scan scratch");
+        h->pair_scratch_bytes = need;
+    }
+    double* d_s = reinterpret_cast<double*>(static_cast<char*>(h->d_pair_scratch) + sel);
+    int32_t* d_pairs = reinterpret_cast<int32_t*>(d_s + top_k);
+    CK(cudaEventRecord(h->ev[0], h->stream), "event");
+    CK(launch_pair_scan(h->ptab, h->k2.lf64, h->M, top_k, h->d_pair_scratch, d_pairs, d_s,
+                        h->stream), "pair scan launch");
+    CK(cudaEventRecord(h->ev[1], h->stream), "event");
+    const cudaMemcpyKind kind =
+        (h->flags & EPI3_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(out_pairs, d_pairs, sizeof(int32_t) * 2 * top_k, kind, h->stream),
+       "copy pairs");
+    CK(cudaMemcpyAsync(out_scores, d_s, sizeof(double) * top_k, kind, h->stream), "copy scores");
+    CK(cudaStreamSynchronize(h->stream), "pair scan");
+    epi3_stats& s = h->stats;
+    s.n_triplets = np;  // pairs scored
+    s.n_candidates = 0;
+    s.n_rescored = np;
+    s.path = EPI3_PATH_AUTO;
+    cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[0], h->ev[1]);
+    s.total_ms = s.scan_kernel_ms;
+    s.select_ms = 0.f;
+    (void)cudaGetLastError();
+    return EPI3_OK;
 }
 
 int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,

@@ -109,6 +109,10 @@ cudaError_t launch_tables(const Planes& pl, const PairTables* pt, const K2Tables
                           const int* trip, int* out_counts, float* out_s32, double* out_s64,
                           Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
+// Pairwise scan (Eq. 1 for two SNPs): the k best pairs by (FP64 K2, i, j) from the pair tables.
+size_t pair_scan_scratch(long long n_pairs, int k);
+cudaError_t launch_pair_scan(const PairTables& pt, const double* lf64, int M, int k,
+                             void* scratch, int32_t* out_pairs, double* out_s, cudaStream_t st);
 // max over n in [0, n_lf) of (n + 1/2) |lg2_hw(n + 1) - log2(n + 1)| (FP64) into *out (device).
 cudaError_t launch_approx_error(const double* lf64, int n_lf, double* out, cudaStream_t st);
 cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long n_pairs,

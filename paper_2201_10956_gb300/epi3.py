@@ -25,7 +25,8 @@ PATH_AUTO, PATH_POPC, PATH_POPC8, PATH_MMA, PATH_MMA16, PATH_MMA4 = 0, 1, 2, 3, 
 MAX_TOPK = 512
 
 # Every symbol the header declares; tests check the library exports all of them.
-SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_destroy", "epi3_last_error",
+SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_scan_pairs", "epi3_destroy",
+           "epi3_last_error",
            "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
            "epi3_scan_noalloc", "epi3_scan_scores", "epi3_batch_create", "epi3_batch_scan",
            "epi3_batch_destroy", "epi3_batch_get_stats", "epi3_batch_get_paths", "epi3_scan_batch")
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         "epi3_create": [ctypes.POINTER(P), P, P, I32, I32, I32, P],
         "epi3_scan": [P, I32, P, P],
         "epi3_scan_range": [P, I64, I64, I32, P, P, ctypes.POINTER(I32)],
+        "epi3_scan_pairs": [P, I32, P, P],
         "epi3_destroy": [P],
         "epi3_last_error": [],
         "epi3_tables": [P, I64, P, P, I32],
@@ -200,6 +202,13 @@ class Handle:
         _check(load().epi3_scan_range(self._h, int(pair_begin), int(pair_end), int(top_k),
                                       _ptr(trip), _ptr(sc), ctypes.byref(n)))
         return trip[: n.value], sc[: n.value]
+
+    def scan_pairs(self, top_k: int):
+        """Pairwise scan (Eq. 1 for two SNPs): top-k pairs (int32 [k, 2]) and FP64 K2 ([k])."""
+        pairs = self._alloc((top_k, 2), np.int32)
+        sc = self._alloc((top_k,), np.float64)
+        _check(load().epi3_scan_pairs(self._h, int(top_k), _ptr(pairs), _ptr(sc)))
+        return pairs, sc
 
     def tables(self, triplets, path: int = PATH_AUTO):
         t = self._triplets(triplets)
