@@ -177,3 +177,17 @@ def test_tensor_scan_full_size_matches_popc8(name):
     assert np.array_equal(tr, ref_t) and np.array_equal(sc, ref_s)
     assert np.array_equal(oracle.scores(g, ph, tr), sc)
     assert tuple(tr[0]) in [tuple(p) for p in d.planted]
+
+
+@pytest.mark.parametrize("name", ["mma4", "popc8"])
+def test_largest_sample_count(name):
+    # 131 072 samples, the most a handle takes: the widest log-factorial table, the loosest
+    # pruning bound and 512 K-steps per class boundary; top-k still equals the oracle's
+    g, ph = pins.tiny_data(9, 131072, 50000, seed=91)
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", name)
+        tr, sc = h.scan(20)
+        if name == "mma4":
+            assert 0.0 < h.stats()["k2_prune_bound"] < 256.0
+    otr, osc, _ = oracle.scan_topk(g, ph, 20)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
