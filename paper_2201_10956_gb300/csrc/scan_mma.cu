@@ -10,22 +10,28 @@
 // Sec. IV; its related work, Sec. II, points at tensor-core formulations.)
 //
 // Tile = (i, 32 second SNPs, 64 third SNPs): MMA M = 128 rows (j, a, b), N = 128 columns
-// (k, z), K = 128 samples (FP8 E4M3 operands) or 64 samples (FP16) per stage, four
-// tcgen05.mma per stage.  The one-hot matrix is pre-tiled in HBM in the exact 128B-swizzled
-// shared-memory image; per stage cp.async.bulk fetches the third-SNP chunk (the MMA's B
-// operand, read from shared memory), the one-hot rows of the second SNPs (Y) and of the
-// first SNP (X).  Four producer warps form A = Y AND X in registers and store it straight
-// into tensor memory (tcgen05.st), where the MMA reads it: the product never passes through
-// shared memory, whose bandwidth bounds this kernel.
+// (k, z), four tcgen05.mma per step; a step is 256 samples with block-scaled FP4 E2M1
+// operands (kind::mxf4, two samples per byte, every scale 2^0), 128 with FP8 E4M3
+// (kind::f8f6f4) or 64 with FP16 (kind::f16).  The one-hot matrix is pre-tiled in HBM in the
+// exact 128B-swizzled shared-memory image; per step cp.async.bulk fetches the third-SNP chunk
+// (the MMA's B operand, read from shared memory), the one-hot rows of the second SNPs (Y) and
+// of the first SNP (X).  Four producer warps form A = Y AND X in registers and store it
+// straight into tensor memory (tcgen05.st), where the MMA reads it: the product never passes
+// through shared memory, whose bandwidth bounded the first design of this kernel.
 //
 // Tensor memory (512 columns): a ring of three 128-column accumulator regions, one per
 // (tile, class) segment, so the epilogue of a tile overlaps the next tile's first class;
-// then four 32-column A stages.
+// then the A stages (32 columns each: four, or three beside the E2M1 block-scale columns).
+// Shared memory: a ring of TMEM stages + 2 steps, the epilogue's candidate buffer and its
+// per-warp transpose slabs.
 //
-// Warp roles (14 warps): 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 =
-// epilogue (two warps per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM
-// lane).  Every mbarrier wait is bounded; on timeout the kernel records kStTimeout, waits
-// for its own bulk copies, frees TMEM and returns.
+// Warp roles (14 warps): 0 = operand loader + TMEM allocator, 1 = MMA issuer (one wait and
+// one commit per step), 2..9 = epilogue (two warps per TMEM lane quadrant; pair-table rows,
+// TMEM read, transpose, derive27, a table-free bound that skips tables above the candidate
+// band, exact FP32 K2 for the rest), 10..13 = A producers (one thread per TMEM lane; they also
+// return each shared-memory stage to the loader once its MMAs are complete).  Every mbarrier
+// wait is bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
+// frees TMEM and returns.
 #include "epi3_internal.cuh"
 
 namespace epi3 {
