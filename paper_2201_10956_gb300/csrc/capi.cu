@@ -192,8 +192,9 @@ int build_k2_tables(epi3_handle* h) {
     // Pruning bound of the tensor scan: |k2_approx - s32| for any table of this data set.
     //   delta  measured max of (n + 1/2) |lg2_hw(n+1) - log2(n+1)| over n = 0..N+1
     //   Stirling remainders: at most 1/6 per cell (e(r+1) - e(r0) - e(r1), 0 < e <= 1/12)
-    //   FMA chain (81 steps, log2 units): each rounds by at most 2^-24 |acc|; every finished
-    //     cell adds a positive amount (its K2 term + ln(2 pi)/2 - Stirling remainder), so
+    //   FMA chains (81 steps in two chains over disjoint cells, then one add; log2 units):
+    //     each of the 82 roundings is at most 2^-24 |acc|; every finished cell adds a positive
+    //     amount (its K2 term + ln(2 pi)/2 - Stirling remainder), so every partial sum obeys
     //     0 <= acc <= (K + 27 (ln(2 pi)/2 + 1/12)) / ln2 + T + 81 delta, with K = 27 ln(N+2)
     //     + N ln 2 bounding K2 and T = (N + 3/2) log2(N + 2) the largest single product
     //   final FMA and the FP32 constants: 2^-22 (K + 27 ln(2 pi)/2 + ln2 (K/ln2 + T))
@@ -213,7 +214,7 @@ int build_k2_tables(epi3_handle* h) {
     const double tmax = ((double)h->N + 1.5) * std::log2((double)h->N + 2.0);
     const double amax = (kmax + 27.0 * (0.9189385332046727 + 1.0 / 12.0)) / ln2 + tmax +
                         81.0 * delta;
-    const double d_approx = 27.0 / 6.0 + ln2 * (81.0 * delta + 81.0 * u * amax) +
+    const double d_approx = 27.0 / 6.0 + ln2 * (81.0 * delta + 82.0 * u * amax) +
                             4.0 * u * (kmax + 27.0 * 0.9189385332046727 + ln2 * amax);
     const double d_s32 = (double)h->k2.rel * kmax + (double)h->k2.abs_;
     h->k2.prune_delta = (float)(2.0 * (d_approx + d_s32) + 0.5);
@@ -317,7 +318,8 @@ int ensure_onehot(epi3_handle* h, int kind) {
     cudaFree(h->d_oh);
     h->d_oh = nullptr;
     const int spk = mma_samples_per_step(kind);
-    const int ks0 = (h->N0 + spk - 1) / spk, ks1 = (h->N1 + spk - 1) / spk;
+    // N_c samples plus the bias sample (position N_c) of a non-empty class
+    const int ks0 = h->N0 ? h->N0 / spk + 1 : 0, ks1 = h->N1 ? h->N1 / spk + 1 : 0;
     const int kbc = (h->M + 63) / 64;
     const size_t bytes = (size_t)kbc * (ks0 + ks1) * 16384;
     CK(dev_alloc((void**)&h->d_oh, bytes), "alloc one-hot operand");

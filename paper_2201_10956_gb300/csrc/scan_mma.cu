@@ -263,7 +263,7 @@ __device__ __forceinline__ uint4 unit_of_bits(uint32_t b) {
 }
 
 // Sample bits of one-hot row (c, p, m) for K-step ks, 32 per word in sample order (w[0..7];
-// words past the step, the class or the SNPs stay 0).
+// words past the step, the class or the SNPs stay 0, except the class's bias sample).
 template <int kKind>
 __device__ __forceinline__ void step_words(const Planes& pl, int c, int p, int m, int ks,
                                            uint32_t* w) {
@@ -290,6 +290,13 @@ __device__ __forceinline__ void step_words(const Planes& pl, int c, int p, int m
         w[0] = (ks & 1) ? g.z : g.x;
         w[1] = (ks & 1) ? g.w : g.y;
     }
+    // the bias sample at class position N_c: a 1 in every row, so every accumulator of the
+    // class ends at count + 1 (the K-steps of a class always leave room for it)
+    const int sps = kKind == kKindE2M1 ? 256 : (kKind == kKindE4M3 ? 128 : 64);
+    const int bias = 128 * pl.W4[c] - pl.pad[c] - ks * sps;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (bias >= 32 * t && bias < 32 * t + 32 && bias < sps) w[t] |= 1u << (bias & 31);
 }
 
 // The 128 bytes of one operand row (r of the chunk) in the 128B-swizzled image.
@@ -303,6 +310,117 @@ __device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint3
         else b = (w[u >> 2] >> ((u & 3) * 8)) & 0xFFu;
         *reinterpret_cast<uint4*>(tile + sw128_off(r, u)) = unit_of_bits<kKind>(b);
     }
+}
+
+// ------------------------------------------------------------------ epilogue arithmetic
+// Every class carries one extra "bias" sample (position N_c, one-hot 1 in every row of every
+// SNP), so each accumulator holds u = count + 1.  The epilogue works on u throughout: the
+// Stirling terms below need exactly count + 1, and an empty class reads as u = 1.  All values
+// are integers below 2^24, so every float add and subtract here is exact.
+
+// x + off as FP32, exact for 0 <= x < 2^23 and small off (x lands in the mantissa of 2^23).
+__device__ __forceinline__ float count_plus(int x, float off) {
+    return __fsub_rn(__int_as_float(x | 0x4B000000), 8388608.0f - off);
+}
+
+// Per (i, j) row of a tile and class: the constants of the derived cells, each + 3 (two
+// u-values of count + 1 are subtracted from a count + 1).
+struct RowCells {
+    float xy[4];      // #(X = a, Y = b) + 3, index 2a + b
+    float xa2[2];     // #(X = a, Y = 2) + 3
+    float x2b[2];     // #(X = 2, Y = b) + 3
+    float c22;        // #(X = 2, Y = 2) + 3
+};
+
+__device__ __forceinline__ RowCells row_cells(int4 pxy, int2 mx, int2 my, int nc) {
+    RowCells rc;
+    const int xa2_0 = mx.x - pxy.x - pxy.y, xa2_1 = mx.y - pxy.z - pxy.w;
+    const int x2b_0 = my.x - pxy.x - pxy.z, x2b_1 = my.y - pxy.y - pxy.w;
+    rc.xy[0] = count_plus(pxy.x, 3.f);
+    rc.xy[1] = count_plus(pxy.y, 3.f);
+    rc.xy[2] = count_plus(pxy.z, 3.f);
+    rc.xy[3] = count_plus(pxy.w, 3.f);
+    rc.xa2[0] = count_plus(xa2_0, 3.f);
+    rc.xa2[1] = count_plus(xa2_1, 3.f);
+    rc.x2b[0] = count_plus(x2b_0, 3.f);
+    rc.x2b[1] = count_plus(x2b_1, 3.f);
+    rc.c22 = count_plus(nc - mx.x - mx.y - x2b_0 - x2b_1, 3.f);
+    return rc;
+}
+
+// u[9 gX + 3 gY + gZ] = cell count + 1 of one class, from the 8 accumulated cells
+// n8[4a + 2b + z] (already + 1) and the pair tables (X, Z), (Y, Z) and marginal of Z:
+// the inclusion-exclusion of derive27 with every term shifted by one.
+__device__ __forceinline__ void cells_u(const float* n8, const RowCells& rc, int4 pxz, int4 pyz,
+                                        int2 mz, float* u) {
+    const float xz[2][2] = {{count_plus(pxz.x, 3.f), count_plus(pxz.y, 3.f)},
+                            {count_plus(pxz.z, 3.f), count_plus(pxz.w, 3.f)}};
+    const float yz[2][2] = {{count_plus(pyz.x, 3.f), count_plus(pyz.y, 3.f)},
+                            {count_plus(pyz.z, 3.f), count_plus(pyz.w, 3.f)}};
+    // #(X = 2, Z = z) + 3 = (#(Z = z) + 9) - (#(X=0, Z=z) + 3) - (#(X=1, Z=z) + 3)
+    const float z2[2] = {__fsub_rn(__fsub_rn(count_plus(mz.x, 9.f), xz[0][0]), xz[1][0]),
+                         __fsub_rn(__fsub_rn(count_plus(mz.y, 9.f), xz[0][1]), xz[1][1])};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
+            u[9 * a + 3 * b] = c0;
+            u[9 * a + 3 * b + 1] = c1;
+            u[9 * a + 3 * b + 2] = __fsub_rn(__fsub_rn(rc.xy[2 * a + b], c0), c1);       // (a,b,2)
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int z = 0; z < 2; ++z)                                                       // (a,2,z)
+            u[9 * a + 6 + z] = __fsub_rn(__fsub_rn(xz[a][z], u[9 * a + z]), u[9 * a + 3 + z]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int z = 0; z < 2; ++z)                                                       // (2,b,z)
+            u[18 + 3 * b + z] = __fsub_rn(__fsub_rn(yz[b][z], u[3 * b + z]), u[9 + 3 * b + z]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)                                                           // (a,2,2)
+        u[9 * a + 8] = __fsub_rn(__fsub_rn(rc.xa2[a], u[9 * a + 6]), u[9 * a + 7]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)                                                           // (2,b,2)
+        u[18 + 3 * b + 2] = __fsub_rn(__fsub_rn(rc.x2b[b], u[18 + 3 * b]), u[18 + 3 * b + 1]);
+#pragma unroll
+    for (int z = 0; z < 2; ++z)                                                           // (2,2,z)
+        u[24 + z] = __fsub_rn(__fsub_rn(z2[z], u[18 + z]), u[21 + z]);
+    u[26] = __fsub_rn(__fsub_rn(rc.c22, u[24]), u[25]);                                   // (2,2,2)
+}
+
+// The table-free K2 approximation of k2_approx on u = count + 1 (same products: u - 1/2 =
+// n + 1/2, lg2(u) = lg2(n + 1), and for the cell sum u0 + u1 = r + 2), in two interleaved
+// FMA chains (cells 0..13 and 14..26) joined by one add.
+__device__ __forceinline__ float k2_bound_u(const float* u0, const float* u1) {
+    float acc[2] = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < kCells; ++q) {
+        float& a = acc[q < 14 ? 0 : 1];
+        const float us = __fadd_rn(u0[q], u1[q]);
+        a = __fmaf_rn(__fsub_rn(us, 0.5f), lg2_hw(us), a);
+        a = __fmaf_rn(-__fsub_rn(u0[q], 0.5f), lg2_hw(u0[q]), a);
+        a = __fmaf_rn(-__fsub_rn(u1[q], 0.5f), lg2_hw(u1[q]), a);
+    }
+    return __fmaf_rn(0.6931471805599453f, __fadd_rn(acc[0], acc[1]), -27.f * 0.9189385332046727f);
+}
+
+// Exact integer cells r = u - 1 of both classes; false unless every cell lies in [0, N_c]
+// (which keeps every log-factorial lookup of the table in range).
+__device__ __forceinline__ bool counts_of(const float* u0, const float* u1, int n0, int n1,
+                                          int* r0, int* r1) {
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < kCells; ++q) {
+        // u + 2^23 - 1 holds u - 1 in its mantissa for 1 <= u < 2^23; anything else falls
+        // outside [0, N_c]
+        r0[q] = __float_as_int(__fadd_rn(u0[q], 8388607.0f)) - 0x4B000000;
+        r1[q] = __float_as_int(__fadd_rn(u1[q], 8388607.0f)) - 0x4B000000;
+        ok = ok && (unsigned)r0[q] <= (unsigned)n0 && (unsigned)r1[q] <= (unsigned)n1;
+    }
+    return ok;
 }
 
 __device__ void sort_cands_epi(Cand* buf, int tid) {
@@ -759,6 +877,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             }
             mx[0] = __ldg(pt.marg + i);
             mx[1] = __ldg(pt.marg + M + i);
+            const RowCells rcl[2] = {row_cells(pxy[0], mx[0], my[0], pt.n_c[0]),
+                                     row_cells(pxy[1], mx[1], my[1], pt.n_c[1])};
             const int reg0 = rR.s;
             ring_next(rR, kRegions);
             const int reg1 = rR.s;
@@ -795,14 +915,16 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
 #pragma unroll
                 for (int c = 0; c < 2; ++c) tc_ld16(tmem + lane_base + rc[c] + 16 * g, v[c]);
                 tc_wait_ld();
-                // n8[c][m][4a + 2b + z] for this lane's third SNPs kk = 8 g + 2 me + m
-                int n8[2][2][8];
+                // n8[c][m][4a + 2b + z] = count + 1 for this lane's third SNPs kk = 8 g + 2 me + m
+                // (the accumulators include the bias sample; a class without samples has no
+                // K-steps and reads as 1)
+                float n8[2][2][8];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const bool has = c ? KS1 > 0 : KS0 > 0;
-                    int x[16];
+                    uint32_t x[16];
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) x[t] = has ? __float2int_rn(__uint_as_float(v[c][t])) : 0;
+                    for (int t = 0; t < 16; ++t) x[t] = has ? v[c][t] : 0x3F800000u;
                     // x[4 blk + e]: column 16 g + 4 blk + e; lane `me` needs block `me` of all
                     // four lanes of its jj.  Through this warp's shared-memory slab: row = lane,
                     // 16-byte unit = block (rows 80 bytes apart, so neither the stores nor the
@@ -810,12 +932,12 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     __syncwarp();  // the previous class's loads are done
 #pragma unroll
                     for (int blk = 0; blk < 4; ++blk)
-                        *reinterpret_cast<int4*>(tw + lane * kTRow + blk * 16) =
-                            make_int4(x[4 * blk], x[4 * blk + 1], x[4 * blk + 2], x[4 * blk + 3]);
+                        *reinterpret_cast<uint4*>(tw + lane * kTRow + blk * 16) =
+                            make_uint4(x[4 * blk], x[4 * blk + 1], x[4 * blk + 2], x[4 * blk + 3]);
                     __syncwarp();
 #pragma unroll
                     for (int src = 0; src < 4; ++src) {
-                        const int4 q = *reinterpret_cast<const int4*>(
+                        const float4 q = *reinterpret_cast<const float4*>(
                             tw + (4 * (lane >> 2) + src) * kTRow + me * 16);
                         n8[c][0][2 * src] = q.x;      // (m = 0, z = 0)
                         n8[c][0][2 * src + 1] = q.y;  // (m = 0, z = 1)
@@ -827,25 +949,21 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 for (int m = 0; m < 2; ++m) {
                     const int k = kb0 + 8 * g + 2 * me + m;
                     if (!(jrow && k > j && k < M)) continue;
-                    int r0[kCells], r1[kCells];
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-                        derive27(n8[c][m], pxy[c], tik[m][c], tjk[m][c], mx[c], my[c], tmk[m][c],
-                                 pt.n_c[c], c ? r1 : r0);
-                    // guard the log-factorial lookups: derive27 makes every class sum N_c, so
-                    // no negative cell means every cell lies in [0, N_c]
-                    int neg = 0;
-#pragma unroll
-                    for (int q = 0; q < kCells; ++q) neg |= r0[q] | r1[q];
-                    if (neg < 0) {
-                        atomicOr(&ctrl->status, kStBadCount);
-                        continue;
-                    }
+                    float u0[kCells], u1[kCells];
+                    cells_u(n8[0][m], rcl[0], tik[m][0], tjk[m][0], tmk[m][0], u0);
+                    cells_u(n8[1][m], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
                     // most tables lie far above the band: prove it from the table-free
                     // approximation and skip the exact score's 81 log-table gathers
                     if (!dbg && prune > 0.f &&
-                        __fsub_rn(k2_approx(r0, r1), prune) > fminf(es.tloc, thr_g))
+                        __fsub_rn(k2_bound_u(u0, u1), prune) > fminf(es.tloc, thr_g))
                         continue;
+                    // exact integer table; a cell outside [0, N_c] would mean a corrupt count
+                    // and is reported instead of looked up
+                    int r0[kCells], r1[kCells];
+                    if (!counts_of(u0, u1, pt.n_c[0], pt.n_c[1], r0, r1)) {
+                        atomicOr(&ctrl->status, kStBadCount);
+                        continue;
+                    }
                     const float s = k2_f32(r0, r1, lf2);
                     if (dbg) dbg[((size_t)i * M + j) * M + k] = s;
                     if (s <= fminf(es.tloc, thr_g)) {
