@@ -484,7 +484,8 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
             CK(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), h->stream), "clear profile");
         }
         CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, kind, grid, h->stream,
-                           h->profile ? h->d_prof : nullptr), "mma scan launch");
+                           h->profile ? h->d_prof : nullptr, mma_split_registers(h->N, kind)),
+           "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
         if (rc == 1) continue;
@@ -499,7 +500,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.n_rescored = h->h_ctrl->n_final;
     s.path = path;
     s.grid = grid;
-    s.block = 448;
+    s.block = mma_threads(mma_split_registers(h->N, kind_of_path(path)));
     s.kernel_launches = 5;
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
     s.wait_producers_tmem = s.mma_issue = 0.f;
@@ -945,6 +946,7 @@ struct epi3_batch {
     CohortDev* d_cds = nullptr;
     int4* d_tiles = nullptr;
     long long n_tiles = 0;
+    bool split = false;                 // register-split form of the tensor scan
     double* d_scores = nullptr;         // [n][EPI3_MAX_TOPK]
     int* d_trip = nullptr;
     double* h_scores = nullptr;         // pinned
@@ -1112,7 +1114,8 @@ int batch_capture(epi3_batch* b, int top_k) {
     cur = "tensor scan";
     cur_c = -1;
     if (b->n_tiles > 0)
-        ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, kKindE2M1, b->sm_count, b->stream));
+        ok(launch_scan_mma(b->d_cds, b->d_tiles, b->n_tiles, kKindE2M1, b->sm_count, b->stream,
+                           nullptr, b->split));
     cur = "popc8 scan";
     for (int c = 0; c < b->n; ++c) {
         if (b->path[c] != EPI3_PATH_POPC8) continue;
@@ -1237,16 +1240,20 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
         if ((rc = ensure_pair_tables(h)) != EPI3_OK) return bail(rc);
     }
     std::vector<int4> tiles;
+    double tile_samples = 0.0;          // sum over the tiles of their data set's samples
     for (int c = 0; c < n_cohorts; ++c) {
         epi3_handle* h = b->h[c];
         if ((rc = tune_path(b, h, &b->path[c], &b->tune_ms)) != EPI3_OK) return bail(rc);
         if (b->path[c] == EPI3_PATH_MMA4) {
             if ((rc = ensure_onehot(h, kKindE2M1)) != EPI3_OK) return bail(rc);
+            const size_t before = tiles.size();
             append_tiles(h->M, 0, pairs(h->M - 1), c, tiles);
+            tile_samples += (double)(tiles.size() - before) * h->N;
         }
         h->path = b->path[c];
     }
     b->n_tiles = (long long)tiles.size();
+    b->split = !tiles.empty() && mma_split_registers(tile_samples / (double)tiles.size(), kKindE2M1);
     if ((e = dev_alloc((void**)&b->d_tiles, sizeof(int4) * (tiles.empty() ? 1 : tiles.size()))) != cudaSuccess)
         return bail(cuda_fail(e, "alloc tiles"));
     if (!tiles.empty() &&
@@ -1341,7 +1348,7 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
     }
     s.path = n_mma == b->n ? EPI3_PATH_MMA4 : (n_mma == 0 ? EPI3_PATH_POPC8 : EPI3_PATH_AUTO);
     s.grid = b->sm_count;
-    s.block = 448;
+    s.block = mma_threads(b->split);
     s.kernel_launches = b->n + (b->n_tiles > 0 ? 1 : 0) + (b->n - n_mma) + 3 * b->n;
     // device time of the whole graph replay (scan kernels + candidate stages + read-back);
     // the scan kernels are > 99 % of it

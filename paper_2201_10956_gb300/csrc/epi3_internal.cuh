@@ -145,8 +145,13 @@ struct CohortDev {
 };
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
+// split: the register-split form of the kernel (mma_split_registers of the launch's samples
+// per data set, for a batch their mean weighted by tiles)
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                            int kind, int grid, cudaStream_t st, unsigned long long* prof = nullptr);
+                            int kind, int grid, cudaStream_t st, unsigned long long* prof,
+                            bool split);
+bool mma_split_registers(double samples, int kind);
+int mma_threads(bool split);   // threads per CTA of the tensor-core scan
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 
 // Message returned by epi3_last_error() on this thread.

@@ -44,12 +44,30 @@ constexpr int kJB = 32;                  // second SNPs per tile (A rows = 4 per
 // a stage goes back to the loader only once its step's MMAs (kTm steps earlier) are complete
 constexpr int kSmStagesMax = 6;
 constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
-// 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA issuer, 2..9 = epilogue (two warps
-// per TMEM lane quadrant), 10..13 = A producers (one thread per TMEM lane).
-constexpr int kThreads = 448;
+// Warp roles, two layouts.  Plain form, 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA
+// issuer, 2..9 = epilogue (two warps per TMEM lane quadrant), 10..13 = A producers (one thread
+// per TMEM lane); every warp has the 128 registers the 14 warps can have.  Register-split
+// form, 16 warps in four warp groups: 0 = loader, 1 = MMA issuer (2, 3 idle), 4..7 =
+// producers, 8..15 = epilogue; launched with 128 registers per thread (all 65536), after which
+// the groups trade them, kRegCtl + kRegProd + 2 kRegEpi = 4 x 128 per thread slot, so that the
+// epilogue's working set fits without spills.  The split pays where the epilogue bounds the
+// scan (few samples per triplet); with many samples the MMA pipeline bounds it and the plain
+// form is faster.
 constexpr int kWarpMma = 1;
-constexpr int kEpiWarp0 = 2, kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
-constexpr int kProdWarp0 = 10, kProdWarps = 4;
+constexpr int kProdWarps = 4;
+constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;
+template <bool kSplit>
+__host__ __device__ constexpr int threads_of() { return kSplit ? 512 : 448; }
+template <bool kSplit>
+__host__ __device__ constexpr int prod_warp0() { return kSplit ? 4 : 10; }
+template <bool kSplit>
+__host__ __device__ constexpr int epi_warp0() { return kSplit ? 8 : 2; }
+constexpr int kRegLaunch = 128, kRegCtl = 56, kRegProd = 104, kRegEpi = 176;
+static_assert(kRegCtl + kRegProd + 2 * kRegEpi == 4 * kRegLaunch, "register split");
+static_assert(threads_of<true>() * kRegLaunch == 65536, "the split launch holds the whole register file");
+// the split form for data sets with fewer samples than this in E2M1 (measured crossover: the
+// split is 7 % faster at 8192 samples and 1.4 % slower at 16384)
+constexpr double kSplitBelow = 14336.0;
 constexpr int kYChunk = kChunk / 2;      // one-hot rows (j, b) of 32 second SNPs: 64 rows
 constexpr int kXBytes = 256;             // one-hot rows (i, 0) and (i, 1): 2 rows
 constexpr int kTmemCols = 512;
@@ -549,8 +567,8 @@ __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds
     cursor_load(cu, cds, tiles, my_tiles);
 }
 
-template <int kKind, bool kProf>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int kKind, bool kProf, bool kSplit>
+__global__ void __launch_bounds__(threads_of<kSplit>(), 1)
 scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tiles, long long n_tiles,
                 unsigned long long* __restrict__ prof) {
     // prof (optional): per role, cycles spent waiting, summed over CTAs:
@@ -582,6 +600,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         (reinterpret_cast<uintptr_t>(&es) + sizeof(EpiShared) + 15) & ~static_cast<uintptr_t>(15));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kProdWarp0 = prod_warp0<kSplit>(), kEpiWarp0 = epi_warp0<kSplit>();
+    const bool is_ctl = kSplit ? warp < kProdWarp0 : warp < kEpiWarp0;
+    const bool is_prod = warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps;
     const uint32_t fullS0 = smem_u32(bars), emptyS0 = smem_u32(bars + kSmStages),
                    fullT0 = smem_u32(bars + 2 * kSmStages),
                    emptyT0 = smem_u32(bars + 2 * kSmStages + kTmStagesMax),
@@ -623,122 +644,126 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         atomicOr(&cd->ctrl->status, kStTimeout);
     };
 
-    if (warp == 0) {
-        // ------------------------------------------------ operand loader (lane 0)
-        if (lane == 0) {
-            StepCursor cu{};
-            cu.tl = 0;
-            cursor_load(cu, cds, tiles, my_tiles);
-            long long q = 0;
-            Ring rs{0, 0u};
-            for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
-                const int s = rs.s;
-                if (!mbar_wait_t(emptyS0 + 8 * s, rs.ph ^ 1u, abort_flag, my_acc)) {
-                    fail(cu.cd);
-                    break;
-                }
-                // K: one-hot rows (k, z) of the tile's 64 third SNPs; Y: rows (j, b) of its 32
-                // second SNPs (half of their 64-SNP chunk); X: rows (i, 0), (i, 1).  All three
-                // come from the same pre-tiled one-hot matrix of the class.
-                const long long base_c = cu.c ? cu.cd->oh_off1 : 0;
-                const int nks = cu.c ? cu.ks1 : cu.ks0;
-                const uint8_t* oh = cu.cd->oh;
-                const long long ca = base_c + (long long)cu.tile.z * nks + cu.ks;
-                const long long cy = base_c + (long long)(cu.tile.y >> 1) * nks + cu.ks;
-                const long long cx = base_c + (long long)(cu.tile.x >> 6) * nks + cu.ks;
-                const uint32_t xr = 2u * (uint32_t)(cu.tile.x & 63);
-                const uint32_t fb = fullS0 + 8 * s;
-                mbar_arrive_tx(fb, kChunk + kYChunk + kXBytes);
-                bulk_g2s(smem_u32(sK + s * kChunk), oh + ca * kChunk, kChunk, fb);
-                bulk_g2s(smem_u32(sY + s * kYChunk), oh + cy * kChunk + (cu.tile.y & 1) * kYChunk,
-                         kYChunk, fb);
-                bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
-                         kXBytes, fb);
-                ring_next(rs, kSmStages);
-            }
-            // drain: the copies of the last stages issued must land before the CTA exits
-            for (long long d = (q > kSmStages ? q - kSmStages : 0); d < q; ++d) {
-                const int s = (int)(d % kSmStages);
-                volatile int no_abort = 0;
-                mbar_wait(fullS0 + 8 * s, (unsigned)((d / kSmStages) & 1), &no_abort);
-            }
-        }
-    } else if (warp == kWarpMma) {
-        // ------------------------------------------------ MMA issuer (lane 0)
-        if (lane == 0) {
-            bool ok = true;
-            if (cds[0].inject_timeout) {  // test hook: a wait that can only run out (1 s)
-                if (!mbar_wait(drain0, 0, abort_flag)) fail(cds);
-                ok = false;
-            }
-            // The issuing thread's own instruction latency bounds the step rate, so the loop
-            // keeps its stage addresses and phases as incrementally updated registers.
-            Ring rR{0, 0u};
-            const uint64_t db0 = sw128_desc(smem_u32(sK));
-            uint64_t db = db0;                        // B descriptor of shared-memory stage s
-            int s = 0, t = 0;                         // shared-memory / TMEM stage
-            uint32_t phT = 0, fT = fullT0, eT = emptyT0, ta = tmem + kProdCol0;
-            for (long long tl = 0; tl < my_tiles && ok; ++tl) {
-                const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
-                const CohortDev* cd = cds + tile.w;
-                const int KS[2] = {cd->KS[0], cd->KS[1]};
-                for (int c = 0; c < 2 && ok; ++c) {
-                    // accumulator region of segment (tile, class): a ring of kRegions
-                    if (!mbar_wait_t(regE0 + 8 * rR.s, rR.ph ^ 1u, abort_flag, kProf ? &busy : nullptr)) {
-                        fail(cd);
-                        ok = false;
+    if (is_ctl) {
+        if (kSplit) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegCtl));
+        if (warp == 0) {
+            // ------------------------------------------------ operand loader (lane 0)
+            if (lane == 0) {
+                StepCursor cu{};
+                cu.tl = 0;
+                cursor_load(cu, cds, tiles, my_tiles);
+                long long q = 0;
+                Ring rs{0, 0u};
+                for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
+                    const int s = rs.s;
+                    if (!mbar_wait_t(emptyS0 + 8 * s, rs.ph ^ 1u, abort_flag, my_acc)) {
+                        fail(cu.cd);
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)rR.s * 128u;
-                    ring_next(rR, kRegions);
-                    for (int ks = 0; ks < KS[c]; ++ks) {
-                        // the producers arrive on fullT only after they saw the step's bulk
-                        // copies land (fullS), so one wait covers both operands
-                        if (!mbar_wait_t(fT, phT, abort_flag, my_acc)) {
+                    // K: one-hot rows (k, z) of the tile's 64 third SNPs; Y: rows (j, b) of its 32
+                    // second SNPs (half of their 64-SNP chunk); X: rows (i, 0), (i, 1).  All three
+                    // come from the same pre-tiled one-hot matrix of the class.
+                    const long long base_c = cu.c ? cu.cd->oh_off1 : 0;
+                    const int nks = cu.c ? cu.ks1 : cu.ks0;
+                    const uint8_t* oh = cu.cd->oh;
+                    const long long ca = base_c + (long long)cu.tile.z * nks + cu.ks;
+                    const long long cy = base_c + (long long)(cu.tile.y >> 1) * nks + cu.ks;
+                    const long long cx = base_c + (long long)(cu.tile.x >> 6) * nks + cu.ks;
+                    const uint32_t xr = 2u * (uint32_t)(cu.tile.x & 63);
+                    const uint32_t fb = fullS0 + 8 * s;
+                    mbar_arrive_tx(fb, kChunk + kYChunk + kXBytes);
+                    bulk_g2s(smem_u32(sK + s * kChunk), oh + ca * kChunk, kChunk, fb);
+                    bulk_g2s(smem_u32(sY + s * kYChunk), oh + cy * kChunk + (cu.tile.y & 1) * kYChunk,
+                             kYChunk, fb);
+                    bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
+                             kXBytes, fb);
+                    ring_next(rs, kSmStages);
+                }
+                // drain: the copies of the last stages issued must land before the CTA exits
+                for (long long d = (q > kSmStages ? q - kSmStages : 0); d < q; ++d) {
+                    const int s = (int)(d % kSmStages);
+                    volatile int no_abort = 0;
+                    mbar_wait(fullS0 + 8 * s, (unsigned)((d / kSmStages) & 1), &no_abort);
+                }
+            }
+        } else if (warp == kWarpMma) {
+            // ------------------------------------------------ MMA issuer (lane 0)
+            if (lane == 0) {
+                bool ok = true;
+                if (cds[0].inject_timeout) {  // test hook: a wait that can only run out (1 s)
+                    if (!mbar_wait(drain0, 0, abort_flag)) fail(cds);
+                    ok = false;
+                }
+                // The issuing thread's own instruction latency bounds the step rate, so the loop
+                // keeps its stage addresses and phases as incrementally updated registers.
+                Ring rR{0, 0u};
+                const uint64_t db0 = sw128_desc(smem_u32(sK));
+                uint64_t db = db0;                        // B descriptor of shared-memory stage s
+                int s = 0, t = 0;                         // shared-memory / TMEM stage
+                uint32_t phT = 0, fT = fullT0, eT = emptyT0, ta = tmem + kProdCol0;
+                for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+                    const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
+                    const CohortDev* cd = cds + tile.w;
+                    const int KS[2] = {cd->KS[0], cd->KS[1]};
+                    for (int c = 0; c < 2 && ok; ++c) {
+                        // accumulator region of segment (tile, class): a ring of kRegions
+                        if (!mbar_wait_t(regE0 + 8 * rR.s, rR.ph ^ 1u, abort_flag, kProf ? &busy : nullptr)) {
                             fail(cd);
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const long long t_issue = kProf ? clock64() : 0;
-                        tc_mma_ts<kKind>(d, ta, db, idesc_of<kKind>(), ks > 0 ? 1u : 0u,
-                                         tmem + kSfCol, tmem + kSfCol + 16);
-#pragma unroll
-                        for (int kk = 1; kk < 4; ++kk)  // 32 bytes of K per instruction
-                            tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(), 1u,
+                        const uint32_t d = tmem + (uint32_t)rR.s * 128u;
+                        ring_next(rR, kRegions);
+                        for (int ks = 0; ks < KS[c]; ++ks) {
+                            // the producers arrive on fullT only after they saw the step's bulk
+                            // copies land (fullS), so one wait covers both operands
+                            if (!mbar_wait_t(fT, phT, abort_flag, my_acc)) {
+                                fail(cd);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const long long t_issue = kProf ? clock64() : 0;
+                            tc_mma_ts<kKind>(d, ta, db, idesc_of<kKind>(), ks > 0 ? 1u : 0u,
                                              tmem + kSfCol, tmem + kSfCol + 16);
-                        // one commit per step: its arrival frees the TMEM A stage, and the
-                        // producers then release the shared-memory stage to the loader
-                        tc_commit(eT);
-                        if (kProf) w_acc2 += (unsigned long long)(clock64() - t_issue);
-                        if (++t == kTm) {
-                            t = 0;
-                            phT ^= 1u;
-                            fT = fullT0;
-                            eT = emptyT0;
-                            ta = tmem + kProdCol0;
-                        } else {
-                            fT += 8;
-                            eT += 8;
-                            ta += kProdCols;
-                        }
-                        if (++s == kSmStages) {
-                            s = 0;
-                            db = db0;
-                        } else {
-                            db += (uint64_t)(kChunk >> 4);
+    #pragma unroll
+                            for (int kk = 1; kk < 4; ++kk)  // 32 bytes of K per instruction
+                                tc_mma_ts<kKind>(d, ta + 8 * kk, db + 2 * kk, idesc_of<kKind>(), 1u,
+                                                 tmem + kSfCol, tmem + kSfCol + 16);
+                            // one commit per step: its arrival frees the TMEM A stage, and the
+                            // producers then release the shared-memory stage to the loader
+                            tc_commit(eT);
+                            if (kProf) w_acc2 += (unsigned long long)(clock64() - t_issue);
+                            if (++t == kTm) {
+                                t = 0;
+                                phT ^= 1u;
+                                fT = fullT0;
+                                eT = emptyT0;
+                                ta = tmem + kProdCol0;
+                            } else {
+                                fT += 8;
+                                eT += 8;
+                                ta += kProdCols;
+                            }
+                            if (++s == kSmStages) {
+                                s = 0;
+                                db = db0;
+                            } else {
+                                db += (uint64_t)(kChunk >> 4);
+                            }
                         }
                     }
+                    if (ok) tc_commit(accF0 + 8 * (int)(tl & 1));
                 }
-                if (ok) tc_commit(accF0 + 8 * (int)(tl & 1));
+                // every MMA issued must complete before TMEM is released
+                tc_commit(drain0);
+                volatile int no_abort = 0;
+                mbar_wait(drain0, 0, &no_abort);
             }
-            // every MMA issued must complete before TMEM is released
-            tc_commit(drain0);
-            volatile int no_abort = 0;
-            mbar_wait(drain0, 0, &no_abort);
-        }
-    } else if (warp >= kProdWarp0) {
+    }
+    } else if (is_prod) {
+        if (kSplit) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegProd));
         // ------------------------------------------------ producers: TMEM lane L = (jj, a, b)
         // Product row (j, a, b) = one-hot row (j, b) AND one-hot row (i, a), bit by bit (an
         // element is 1.0 or 0 in every kind, and 1.0 AND 1.0 = 1.0), read from the staged Y and
@@ -826,8 +851,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             __syncwarp();
             if (lane == 0) mbar_arrive(fullT0 + 8 * t_prev);
         }
-    } else if (warp >= kEpiWarp0) {
-        // ------------------------------------------------ epilogue (warps 2..9)
+    } else {
+        if (kSplit) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegEpi));
+        // ------------------------------------------------ epilogue
         // TMEM lane L = (jj, a, b) holds, per class, the counts of (i = a, j = b, k = z) for
         // every column 2 kk + z.  The four lanes of one jj exchange values so that each ends
         // with all 8 cells of two (jj, kk) per 16-column group.
@@ -999,11 +1025,11 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             atomicAdd(prof + 2, busy);
             atomicAdd(prof + 7, w_acc2);
         }
-        if (warp >= kProdWarp0 && lane == 0) {
+        if (is_prod && lane == 0) {
             atomicAdd(prof + 3, w_acc);
             atomicAdd(prof + 6, w_acc2);
         }
-        if (warp >= kEpiWarp0 && warp < kProdWarp0 && lane == 0) atomicAdd(prof + 4, w_acc);
+        if (!is_ctl && !is_prod && lane == 0) atomicAdd(prof + 4, w_acc);
         if (threadIdx.x == 0) atomicAdd(prof + 5, total);
     }
     __syncthreads();
@@ -1069,14 +1095,21 @@ cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0
     return cudaGetLastError();
 }
 
-template <int kKind, bool kProf>
+template <int kKind, bool kProf, bool kSplit>
 static cudaError_t launch_variant(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                                   int grid, cudaStream_t st, unsigned long long* prof) {
     const size_t smem = scan_mma_smem(kKind);
-    const cudaError_t e = cudaFuncSetAttribute(
-        scan_mma_kernel<kKind, kProf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the warp groups' register split adds up to exactly the launch's registers: refuse to
+    // launch a build whose register count differs (its increase could never be granted)
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, scan_mma_kernel<kKind, kProf, kSplit>);
     if (e != cudaSuccess) return e;
-    scan_mma_kernel<kKind, kProf><<<grid, kThreads, smem, st>>>(cohorts, tiles, n_tiles, prof);
+    if (kSplit && fa.numRegs != kRegLaunch) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(scan_mma_kernel<kKind, kProf, kSplit>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    scan_mma_kernel<kKind, kProf, kSplit><<<grid, threads_of<kSplit>(), smem, st>>>(cohorts, tiles,
+                                                                                 n_tiles, prof);
     return cudaGetLastError();
 }
 
@@ -1084,16 +1117,29 @@ static cudaError_t launch_variant(const CohortDev* cohorts, const int4* tiles, l
 // loops carry no clock reads or profiling branches.
 template <int kKind>
 static cudaError_t launch_kind(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                               int grid, cudaStream_t st, unsigned long long* prof) {
-    return prof ? launch_variant<kKind, true>(cohorts, tiles, n_tiles, grid, st, prof)
-                : launch_variant<kKind, false>(cohorts, tiles, n_tiles, grid, st, prof);
+                               int grid, cudaStream_t st, unsigned long long* prof, bool split) {
+    if (split)
+        return prof ? launch_variant<kKind, true, true>(cohorts, tiles, n_tiles, grid, st, prof)
+                    : launch_variant<kKind, false, true>(cohorts, tiles, n_tiles, grid, st, prof);
+    return prof ? launch_variant<kKind, true, false>(cohorts, tiles, n_tiles, grid, st, prof)
+                : launch_variant<kKind, false, false>(cohorts, tiles, n_tiles, grid, st, prof);
 }
 
+bool mma_split_registers(double samples, int kind) {
+    // the crossover scales with the MMA time per sample: 2x (E4M3) and 4x (FP16) that of E2M1
+    return samples * (256.0 / mma_samples_per_step(kind)) < kSplitBelow;
+}
+
+int mma_threads(bool split) { return split ? threads_of<true>() : threads_of<false>(); }
+
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                            int kind, int grid, cudaStream_t st, unsigned long long* prof) {
-    if (kind == kKindE2M1) return launch_kind<kKindE2M1>(cohorts, tiles, n_tiles, grid, st, prof);
-    if (kind == kKindE4M3) return launch_kind<kKindE4M3>(cohorts, tiles, n_tiles, grid, st, prof);
-    return launch_kind<kKindF16>(cohorts, tiles, n_tiles, grid, st, prof);
+                            int kind, int grid, cudaStream_t st, unsigned long long* prof,
+                            bool split) {
+    if (kind == kKindE2M1)
+        return launch_kind<kKindE2M1>(cohorts, tiles, n_tiles, grid, st, prof, split);
+    if (kind == kKindE4M3)
+        return launch_kind<kKindE4M3>(cohorts, tiles, n_tiles, grid, st, prof, split);
+    return launch_kind<kKindF16>(cohorts, tiles, n_tiles, grid, st, prof, split);
 }
 
 }  // namespace epi3
