@@ -425,6 +425,28 @@ __device__ __forceinline__ float k2_bound_u(const float* u0, const float* u1) {
     return __fmaf_rn(0.6931471805599453f, __fadd_rn(acc[0], acc[1]), -27.f * 0.9189385332046727f);
 }
 
+// k2_bound_u of two tables at once (four independent chains), for the register-split form.
+__device__ __forceinline__ void k2_bound_u2(const float* u0a, const float* u1a, const float* u0b,
+                                            const float* u1b, float* out) {
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int q = 0; q < kCells; ++q) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const float x0 = t ? u0b[q] : u0a[q], x1 = t ? u1b[q] : u1a[q];
+            float& a = acc[t][q < 14 ? 0 : 1];
+            const float us = __fadd_rn(x0, x1);
+            a = __fmaf_rn(__fsub_rn(us, 0.5f), lg2_hw(us), a);
+            a = __fmaf_rn(-__fsub_rn(x0, 0.5f), lg2_hw(x0), a);
+            a = __fmaf_rn(-__fsub_rn(x1, 0.5f), lg2_hw(x1), a);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        out[t] = __fmaf_rn(0.6931471805599453f, __fadd_rn(acc[t][0], acc[t][1]),
+                           -27.f * 0.9189385332046727f);
+}
+
 // Exact integer cells r = u - 1 of both classes; false unless every cell lies in [0, N_c]
 // (which keeps every log-factorial lookup of the table in range).
 __device__ __forceinline__ bool counts_of(const float* u0, const float* u1, int n0, int n1,
@@ -971,16 +993,30 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                         n8[c][1][2 * src + 1] = q.w;  // (m = 1, z = 1)
                     }
                 }
+                const bool pruning = !dbg && prune > 0.f;
+                // the split form has the registers to bound both tables of the lane at once
+                // (a lane outside the triangle computes a bound it does not use)
+                float bnd[2] = {0.f, 0.f};
+                if (kSplit && pruning) {
+                    float u0a[kCells], u1a[kCells], u0b[kCells], u1b[kCells];
+                    cells_u(n8[0][0], rcl[0], tik[0][0], tjk[0][0], tmk[0][0], u0a);
+                    cells_u(n8[1][0], rcl[1], tik[0][1], tjk[0][1], tmk[0][1], u1a);
+                    cells_u(n8[0][1], rcl[0], tik[1][0], tjk[1][0], tmk[1][0], u0b);
+                    cells_u(n8[1][1], rcl[1], tik[1][1], tjk[1][1], tmk[1][1], u1b);
+                    k2_bound_u2(u0a, u1a, u0b, u1b, bnd);
+                }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     const int k = kb0 + 8 * g + 2 * me + m;
                     if (!(jrow && k > j && k < M)) continue;
+                    if (kSplit && pruning && __fsub_rn(bnd[m], prune) > fminf(es.tloc, thr_g))
+                        continue;
                     float u0[kCells], u1[kCells];
                     cells_u(n8[0][m], rcl[0], tik[m][0], tjk[m][0], tmk[m][0], u0);
                     cells_u(n8[1][m], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
                     // most tables lie far above the band: prove it from the table-free
                     // approximation and skip the exact score's 81 log-table gathers
-                    if (!dbg && prune > 0.f &&
+                    if (!kSplit && pruning &&
                         __fsub_rn(k2_bound_u(u0, u1), prune) > fminf(es.tloc, thr_g))
                         continue;
                     // exact integer table; a cell outside [0, N_c] would mean a corrupt count
