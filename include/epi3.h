@@ -162,12 +162,16 @@ int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k
 int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
 
 /*
- * Options (strings): "path" = "auto" | "popc" | "popc8" | "mma" | "mma16"; "threads" =
- * threads per block of
- * the scan kernel (64..512, multiple of 32); "ctas_per_sm" = persistent CTAs
- * per SM (0 = occupancy maximum); "timing" = "0" | "1" (record CUDA events
- * around the scan's kernels, read back with epi3_get_stats); "profile" = "0" | "1" (per-role
- * wait accounting inside the tensor-core scan kernel, reported in epi3_stats).
+ * Options (strings): "path" = "auto" | "popc" | "popc8" | "mma" | "mma16" | "mma4";
+ * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
+ * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);
+ * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with
+ * epi3_get_stats); "profile" = "0" | "1" (per-role wait accounting inside the tensor-core
+ * scan kernel, reported in epi3_stats); "mma_form" = "auto" | "plain" | "split" (the
+ * tensor-core scan kernel's form: 14 warps with 128 registers each, or 16 warps that move
+ * registers to the epilogue; "auto" takes the split form below a sample count where the
+ * epilogue bounds the scan).  Unknown keys or values: EPI3_ERR_ARG, or EPI3_ERR_UNSUPPORTED
+ * for a path that is not available.
  */
 int epi3_set_option(epi3_handle* h, const char* key, const char* value);
 

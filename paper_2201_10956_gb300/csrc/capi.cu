@@ -101,6 +101,7 @@ struct epi3_handle {
     float* dbg = nullptr;         // device buffer of epi3_scan_scores (during that call only)
     CohortDev* d_cd = nullptr;    // this data set's descriptor for the tensor-core kernel
     bool profile = false;
+    int mma_form = 0;                    // tensor scan: 0 = by sample count, 1 = plain, 2 = split
     unsigned long long* d_prof = nullptr;
     int4* d_tiles = nullptr;      // tile list of the tensor-core form
     long long n_tiles = 0, tiles_pb = -1, tiles_pe = -1;
@@ -438,6 +439,11 @@ int copy_out(epi3_handle* h, int32_t* out_trip, double* out_scores, int32_t* n_o
     return EPI3_OK;
 }
 
+// Register-split or plain form of the tensor scan for this handle (option "mma_form").
+bool mma_split(const epi3_handle* h, int kind) {
+    return h->mma_form == 0 ? mma_split_registers(h->N, kind) : h->mma_form == 2;
+}
+
 CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k) {
     CohortDev cd{};
     cd.pl = h->pl;
@@ -484,7 +490,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
             CK(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), h->stream), "clear profile");
         }
         CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, kind, grid, h->stream,
-                           h->profile ? h->d_prof : nullptr, mma_split_registers(h->N, kind)),
+                           h->profile ? h->d_prof : nullptr, mma_split(h, kind)),
            "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
@@ -500,7 +506,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.n_rescored = h->h_ctrl->n_final;
     s.path = path;
     s.grid = grid;
-    s.block = mma_threads(mma_split_registers(h->N, kind_of_path(path)));
+    s.block = mma_threads(mma_split(h, kind_of_path(path)));
     s.kernel_launches = 5;
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
     s.wait_producers_tmem = s.mma_issue = 0.f;
@@ -899,6 +905,13 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
     }
     if (!strcmp(key, "profile")) {
         h->profile = atoi(value) != 0;
+        return EPI3_OK;
+    }
+    if (!strcmp(key, "mma_form")) {
+        if (!strcmp(value, "auto")) h->mma_form = 0;
+        else if (!strcmp(value, "plain")) h->mma_form = 1;
+        else if (!strcmp(value, "split")) h->mma_form = 2;
+        else return fail(EPI3_ERR_ARG, "mma_form '%s' not auto, plain or split", value);
         return EPI3_OK;
     }
     if (!strcmp(key, "timing")) {

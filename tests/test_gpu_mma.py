@@ -191,3 +191,22 @@ def test_largest_sample_count(name):
             assert 0.0 < h.stats()["k2_prune_bound"] < 256.0
     otr, osc, _ = oracle.scan_topk(g, ph, 20)
     assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("m,n,n1", [(40, 512, 256), (70, 3000, 1200), (33, 20000, 7000)])
+def test_both_kernel_forms(m, n, n1):
+    # the plain (14 warps) and register-split (16 warps) forms of the tensor scan: every
+    # triplet's table exact in both, identical top-k, and the stats report the launched form
+    g, ph = pins.tiny_data(m, n, n1, seed=400 + m)
+    otr, osc, _ = oracle.scan_topk(g, ph, 12)
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", "mma4")
+        for form, threads in (("plain", 448), ("split", 512)):
+            h.set_option("mma_form", form)
+            check_every_triplet(h, g, ph, epi.PATH_MMA4)
+            tr, sc = h.scan(12)
+            assert h.stats()["block"] == threads
+            assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+        with pytest.raises(epi.Epi3Error) as ei:
+            h.set_option("mma_form", "wide")
+        assert ei.value.code == epi.ERR_ARG
