@@ -190,7 +190,7 @@ int build_k2_tables(epi3_handle* h) {
     h->k2.lf64 = h->d_lf64;
     h->k2.rel = std::ldexp(1.0f, -23);
     h->k2.abs_ = std::ldexp(1.0f, -(g + 13));
-    // Pruning bound of the tensor scan: |k2_approx - s32| for any table of this data set.
+    // Pruning bound of the tensor scan: |K2 bound - s32| for any table of this data set.
     //   delta  measured max of (n + 1/2) |lg2_hw(n+1) - log2(n+1)| over n = 0..N+1
     //   Stirling remainders: at most 1/6 per cell (e(r+1) - e(r0) - e(r1), 0 < e <= 1/12)
     //   FMA chains (81 steps in two chains over disjoint cells, then one add; log2 units):

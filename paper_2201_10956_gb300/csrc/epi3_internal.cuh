@@ -65,7 +65,7 @@ struct K2Tables {
     const float2* lf2;            // lf(n) = hi + lo, hi on a 2^-g grid (exact sums)
     const double* lf64;           // lf(n), same values as the host recurrence
     float rel, abs_;              // |s32 - s64| <= rel * s + abs_
-    // |k2_approx - s32| <= prune_delta for every table of this data set (0: no pruning)
+    // |K2 bound - s32| <= prune_delta for every table of this data set (0: no pruning)
     float prune_delta;
 };
 
@@ -246,13 +246,14 @@ __device__ __forceinline__ float k2_f32(const int* r0, const int* r1, const floa
     return __fadd_rn(ah, al);
 }
 
-// Table-free approximate K2, used only to prove that a table lies above the candidate band.
+// Table-free approximate K2 (the tensor scan's pruning bound), used only to prove that a table
+// lies above the candidate band.
 // Stirling: lf(n) = (n + 1/2) ln(n + 1) - (n + 1) + ln(2 pi)/2 + e(n), 0 < e(n) <= 1/(12(n+1)).
 // In a cell term lf(r+1) - lf(r0) - lf(r1) (r = r0 + r1) the linear parts cancel, so
 //   K2 ~= ln 2 * sum_c [phi(r+1) - phi(r0) - phi(r1)] - 27 ln(2 pi)/2,  phi(n) = (n+1/2) log2(n+1),
-// off by the Stirling remainders (at most 1/6 per cell), by the error of the hardware log2
+// off by the Stirling remainders (at most 1/6 per cell), by the error of this hardware log2
 // inside phi (measured for every n of a data set by launch_approx_error) and by the FP32
-// rounding of the FMA chain.  Every operation is an explicit intrinsic, so the value does not
+// rounding of the FMA chains.  Every operation is an explicit intrinsic, so the value does not
 // depend on the compiler's contraction choices.
 __device__ __forceinline__ float lg2_hw(float x) {
     float y;
@@ -262,18 +263,6 @@ __device__ __forceinline__ float lg2_hw(float x) {
 // n as FP32, exact for 0 <= n < 2^23 (n + 2^23 has the integer in its mantissa)
 __device__ __forceinline__ float exact_float(int n) {
     return __fsub_rn(__int_as_float(n + 0x4B000000), 8388608.0f);
-}
-__device__ __forceinline__ float k2_approx(const int* r0, const int* r1) {
-    float acc = 0.f;
-#pragma unroll
-    for (int c = 0; c < kCells; ++c) {
-        const float x0 = exact_float(r0[c]), x1 = exact_float(r1[c]);
-        const float xs = __fadd_rn(x0, x1);
-        acc = __fmaf_rn(__fadd_rn(xs, 1.5f), lg2_hw(__fadd_rn(xs, 2.f)), acc);
-        acc = __fmaf_rn(-__fadd_rn(x0, 0.5f), lg2_hw(__fadd_rn(x0, 1.f)), acc);
-        acc = __fmaf_rn(-__fadd_rn(x1, 0.5f), lg2_hw(__fadd_rn(x1, 1.f)), acc);
-    }
-    return __fmaf_rn(0.6931471805599453f, acc, -27.f * 0.9189385332046727f);
 }
 
 // FP64 K2 (Eq. 1) in cell order 0..26: term = (lf[r+1] - lf[r0]) - lf[r1], sum from 0.0.

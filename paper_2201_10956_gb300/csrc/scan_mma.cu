@@ -409,9 +409,9 @@ __device__ __forceinline__ void cells_u(const float* n8, const RowCells& rc, int
     u[26] = __fsub_rn(__fsub_rn(rc.c22, u[24]), u[25]);                                   // (2,2,2)
 }
 
-// The table-free K2 approximation of k2_approx on u = count + 1 (same products: u - 1/2 =
-// n + 1/2, lg2(u) = lg2(n + 1), and for the cell sum u0 + u1 = r + 2), in two interleaved
-// FMA chains (cells 0..13 and 14..26) joined by one add.
+// The table-free K2 approximation (Stirling's form, lg2_hw) on u = count + 1: phi(n) =
+// (u - 1/2) lg2(u), and the cell sum's argument is u0 + u1 = r + 2, so no conversion is
+// needed; two interleaved FMA chains (cells 0..13 and 14..26) joined by one add.
 __device__ __forceinline__ float k2_bound_u(const float* u0, const float* u1) {
     float acc[2] = {0.f, 0.f};
 #pragma unroll

@@ -270,7 +270,7 @@ cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Largest error of the products (n + 1/2) * lg2_hw(n + 1) of k2_approx over every n the scan
+// Largest error of the products (n + 1/2) * lg2_hw(n + 1) of the K2 bound over every n the scan
 // can pass (0 .. N+1): the hardware log against FP64 log2, scaled by the exact multiplier.
 __global__ void approx_error_kernel(const double* __restrict__ lf64, int n,
                                     unsigned long long* __restrict__ out) {
