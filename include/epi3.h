@@ -162,6 +162,20 @@ int epi3_scores(epi3_handle* h, int64_t n, const int32_t* triplets, float* out_k
 int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
 
 /*
+ * Debug / test: an order-independent checksum of every table that the scan kernel of `path`
+ * (EPI3_PATH_*) counts in a full scan of the handle's data set (no pruning), so two counting
+ * forms can be compared table by table at any size.  Each triplet i < j < k with class
+ * tables r0[27], r1[27] (cell 9 gX + 3 gY + gZ) contributes
+ *     f = fold over q = 0..26 of  f * 0x100000001B3 + r0[q] + (r1[q] << 32)   (from f = 0),
+ *     hash = mix(f XOR mix((i << 42) | (j << 21) | k)),
+ * mix the splitmix64 finaliser (add 0x9E3779B97F4A7C15; xor-shift 30, multiply
+ * 0xBF58476D1CE4E5B9; xor-shift 27, multiply 0x94D049BB133111EB; xor-shift 31), all modulo
+ * 2^64.  Outputs (host memory): *out_sum = sum of the hashes mod 2^64, *out_count = tables
+ * counted (C(M, 3) for a complete scan).  Errors as epi3_scan.
+ */
+int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t* out_count);
+
+/*
  * Options (strings): "path" = "auto" | "popc" | "popc8" | "mma" | "mma16" | "mma4";
  * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
  * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);

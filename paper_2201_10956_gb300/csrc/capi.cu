@@ -99,6 +99,7 @@ struct epi3_handle {
     int oh_ks[2] = {0, 0};
     long long oh_off1 = 0;
     float* dbg = nullptr;         // device buffer of epi3_scan_scores (during that call only)
+    unsigned long long* tsum = nullptr;  // checksum slots of epi3_scan_checksum (that call only)
     CohortDev* d_cd = nullptr;    // this data set's descriptor for the tensor-core kernel
     bool profile = false;
     int mma_form = 0;                    // tensor scan: 0 = by sample count, 1 = plain, 2 = split
@@ -460,6 +461,7 @@ CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k)
     cd.cand_cap = h->cand_cap;
     cd.top_k = top_k;
     cd.dbg = h->dbg;
+    cd.tsum = h->tsum;
     cd.inject_timeout = inject("timeout") ? 1 : 0;
     return cd;
 }
@@ -490,7 +492,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
             CK(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), h->stream), "clear profile");
         }
         CK(launch_scan_mma(h->d_cd, h->d_tiles, h->n_tiles, kind, grid, h->stream,
-                           h->profile ? h->d_prof : nullptr, mma_split(h, kind)),
+                           h->profile ? h->d_prof : nullptr, mma_split(h, kind), h->tsum != nullptr),
            "mma scan launch");
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
         const int rc = finish_scan(h, top_k, attempt);
@@ -587,6 +589,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         a.pair_end = pe;
         a.top_k = top_k;
         a.dbg = h->dbg;
+        a.tsum = h->tsum;
         CK(cudaEventRecord(h->ev[1], h->stream), "event");
         if (path == EPI3_PATH_POPC8) CK(launch_scan_popc8(a, grid, block, smem, h->stream), "scan launch");
         else CK(launch_scan_popc(a, grid, block, smem, h->stream), "scan launch");
@@ -877,6 +880,41 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores) {
     return rc;
 }
 
+int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t* out_count) {
+    g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
+    if (!h || !out_sum || !out_count) return fail(EPI3_ERR_ARG, "null argument");
+    unsigned long long* d = nullptr;
+    CK(dev_alloc((void**)&d, 2 * kTsumSlots * sizeof(unsigned long long)), "alloc checksum slots");
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * kTsumSlots * sizeof(unsigned long long), h->stream);
+    int rc = e == cudaSuccess ? EPI3_OK : cuda_fail(e, "clear checksum slots");
+    const int saved = h->path;
+    if (rc == EPI3_OK) {
+        h->path = path;
+        h->tsum = d;
+        int32_t trip[3];
+        double sc;
+        rc = scan_impl(h, 0, pairs(h->M), 1, trip, &sc, nullptr, true);
+        h->tsum = nullptr;
+        h->path = saved;
+    }
+    unsigned long long slots[2 * kTsumSlots];
+    if (rc == EPI3_OK) {
+        e = cudaMemcpy(slots, d, sizeof(slots), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "read checksum slots");
+    }
+    cudaFree(d);
+    if (rc != EPI3_OK) return rc;
+    unsigned long long sum = 0, cnt = 0;
+    for (int q = 0; q < kTsumSlots; ++q) {
+        sum += slots[q];
+        cnt += slots[kTsumSlots + q];
+    }
+    *out_sum = sum;
+    *out_count = (int64_t)cnt;
+    return EPI3_OK;
+}
+
 int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
     g_err.clear();
     (void)cudaGetLastError();  // do not report an earlier call's error as ours
@@ -1153,6 +1191,7 @@ int batch_capture(epi3_batch* b, int top_k) {
         a.pair_end = pairs(h->M - 1);
         a.top_k = top_k;
         a.dbg = nullptr;
+        a.tsum = nullptr;
         ok(launch_scan_popc8(a, grid[c], h->threads, smem[c], b->stream));
         if (err != cudaSuccess && where_c == c && !strcmp(where, "popc8 scan")) {
             char buf[160];

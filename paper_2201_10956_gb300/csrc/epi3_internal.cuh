@@ -89,6 +89,7 @@ struct ScanArgs {
     long long pair_begin, pair_end;
     int top_k;
     float* dbg;                   // optional: FP32 score of every triplet at (i*M + j)*M + k
+    unsigned long long* tsum;     // optional: table checksum slots (table_sum), no pruning
 };
 
 // launchers (return cudaError_t of the launch)
@@ -141,15 +142,17 @@ struct CohortDev {
     long long cand_cap;
     int top_k;
     float* dbg;
+    unsigned long long* tsum;     // optional: table checksum slots (table_sum), no pruning
     int inject_timeout;       // test hook: the MMA issuer first waits on a barrier nobody signals
 };
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
 // split: the register-split form of the kernel (mma_split_registers of the launch's samples
 // per data set, for a batch their mean weighted by tiles)
+// checksum: the cohorts' tsum slots are set (the instrumented instantiation adds every table)
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                             int kind, int grid, cudaStream_t st, unsigned long long* prof,
-                            bool split);
+                            bool split, bool checksum = false);
 bool mma_split_registers(double samples, int kind);
 int mma_threads(bool split);   // threads per CTA of the tensor-core scan
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
@@ -263,6 +266,33 @@ __device__ __forceinline__ float lg2_hw(float x) {
 // n as FP32, exact for 0 <= n < 2^23 (n + 2^23 has the integer in its mantissa)
 __device__ __forceinline__ float exact_float(int n) {
     return __fsub_rn(__int_as_float(n + 0x4B000000), 8388608.0f);
+}
+
+// Order-independent checksum of counted tables (debug entry point epi3_scan_checksum): every
+// table's hash(i, j, k, r0, r1) is summed (mod 2^64) by the thread that counted it, and each
+// thread adds its sum and its table count into one of kTsumSlots slot pairs at the end; the
+// host sums the slots.  The hash is the splitmix64 finaliser applied to a multiply-add fold of
+// the 54 counts and to the packed triplet key.
+constexpr int kTsumSlots = 32;
+__host__ __device__ inline unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ inline unsigned long long table_hash(int i, int j, int k, const int* r0, const int* r1) {
+    unsigned long long f = 0;
+    for (int q = 0; q < kCells; ++q)
+        f = f * 0x100000001B3ull + (unsigned long long)(unsigned)r0[q] +
+            ((unsigned long long)(unsigned)r1[q] << 32);
+    return mix64(f ^ mix64(pack_key(i, j, k)));
+}
+__device__ inline void table_sum_flush(unsigned long long* tsum, unsigned long long h,
+                                       unsigned long long n) {
+    if (n == 0) return;
+    const int slot = (int)((threadIdx.x + blockIdx.x) % kTsumSlots);
+    atomicAdd(tsum + slot, h);
+    atomicAdd(tsum + kTsumSlots + slot, n);
 }
 
 // FP64 K2 (Eq. 1) in cell order 0..26: term = (lf[r+1] - lf[r0]) - lf[r1], sum from 0.0.

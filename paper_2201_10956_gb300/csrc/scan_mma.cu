@@ -885,6 +885,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint8_t* tw = sT + (warp - kEpiWarp0) * (32 * kTRow);  // this warp's transpose slab
         int cur = -1;
+        unsigned long long sum_h = 0, sum_n = 0;  // table checksum of this thread (tsum_on)
         Ring rR{0, 0u};
         for (long long tl = 0; tl < my_tiles; ++tl) {
             const int buf = (int)(tl & 1);
@@ -993,7 +994,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                         n8[c][1][2 * src + 1] = q.w;  // (m = 1, z = 1)
                     }
                 }
-                const bool pruning = !dbg && prune > 0.f;
+                // the instrumented instantiation (kProf) also serves table checksums
+                const bool tsum_on = kProf && cd.tsum != nullptr;
+                const bool pruning = !dbg && !tsum_on && prune > 0.f;
                 // the split form has the registers to bound both tables of the lane at once
                 // (a lane outside the triangle computes a bound it does not use)
                 float bnd[2] = {0.f, 0.f};
@@ -1028,6 +1031,10 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     }
                     const float s = k2_f32(r0, r1, lf2);
                     if (dbg) dbg[((size_t)i * M + j) * M + k] = s;
+                    if (tsum_on) {
+                        sum_h += table_hash(i, j, k, r0, r1);
+                        ++sum_n;
+                    }
                     if (s <= fminf(es.tloc, thr_g)) {
                         const int idx = atomicAdd(&es.cnt, 1);
                         if (idx < kCandCapMma) es.buf[idx] = Cand{s, i, j, k};
@@ -1052,8 +1059,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         }
         epi_bar();
         if (cur >= 0) epi_prune(cds[cur], es, min(es.cnt, kCandCapMma), tid, true);
+        if (kProf && cur >= 0 && cds[cur].tsum) table_sum_flush(cds[cur].tsum, sum_h, sum_n);
     }
-    if (kProf) {
+    if (kProf && prof) {
         const unsigned long long total = (unsigned long long)(clock64() - t_start);
         if (warp == 0 && lane == 0) atomicAdd(prof + 0, w_acc);
         if (warp == kWarpMma && lane == 0) {
@@ -1149,16 +1157,17 @@ static cudaError_t launch_variant(const CohortDev* cohorts, const int4* tiles, l
     return cudaGetLastError();
 }
 
-// Role profiling (option "profile") is a separate instantiation, so the normal kernel's hot
-// loops carry no clock reads or profiling branches.
+// Role profiling (option "profile") and table checksums use a separate, instrumented
+// instantiation, so the normal kernel's hot loops carry no clock reads or hooks.
 template <int kKind>
 static cudaError_t launch_kind(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
-                               int grid, cudaStream_t st, unsigned long long* prof, bool split) {
+                               int grid, cudaStream_t st, unsigned long long* prof, bool split,
+                               bool instrument) {
     if (split)
-        return prof ? launch_variant<kKind, true, true>(cohorts, tiles, n_tiles, grid, st, prof)
-                    : launch_variant<kKind, false, true>(cohorts, tiles, n_tiles, grid, st, prof);
-    return prof ? launch_variant<kKind, true, false>(cohorts, tiles, n_tiles, grid, st, prof)
-                : launch_variant<kKind, false, false>(cohorts, tiles, n_tiles, grid, st, prof);
+        return instrument ? launch_variant<kKind, true, true>(cohorts, tiles, n_tiles, grid, st, prof)
+                          : launch_variant<kKind, false, true>(cohorts, tiles, n_tiles, grid, st, prof);
+    return instrument ? launch_variant<kKind, true, false>(cohorts, tiles, n_tiles, grid, st, prof)
+                      : launch_variant<kKind, false, false>(cohorts, tiles, n_tiles, grid, st, prof);
 }
 
 bool mma_split_registers(double samples, int kind) {
@@ -1170,12 +1179,13 @@ int mma_threads(bool split) { return split ? threads_of<true>() : threads_of<fal
 
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                             int kind, int grid, cudaStream_t st, unsigned long long* prof,
-                            bool split) {
+                            bool split, bool checksum) {
+    const bool ins = prof != nullptr || checksum;
     if (kind == kKindE2M1)
-        return launch_kind<kKindE2M1>(cohorts, tiles, n_tiles, grid, st, prof, split);
+        return launch_kind<kKindE2M1>(cohorts, tiles, n_tiles, grid, st, prof, split, ins);
     if (kind == kKindE4M3)
-        return launch_kind<kKindE4M3>(cohorts, tiles, n_tiles, grid, st, prof, split);
-    return launch_kind<kKindF16>(cohorts, tiles, n_tiles, grid, st, prof, split);
+        return launch_kind<kKindE4M3>(cohorts, tiles, n_tiles, grid, st, prof, split, ins);
+    return launch_kind<kKindF16>(cohorts, tiles, n_tiles, grid, st, prof, split, ins);
 }
 
 }  // namespace epi3

@@ -150,8 +150,9 @@ __device__ void flush_cands(const ScanArgs& a, const Cand* buf, int n, float t) 
 
 // kEight = false: the paper's 27-cell count (Alg. 2 with the pair products staged);
 // kEight = true: the 8 cells with genotypes in {0,1} counted, the other 19 derived exactly
-// from the pair tables (derive27).
-template <bool kEight>
+// from the pair tables (derive27).  kSum: the instantiation that also adds every table to the
+// checksum slots a.tsum (epi3_scan_checksum), kept apart so the product kernel carries no hook.
+template <bool kEight, bool kSum>
 __global__ void __launch_bounds__(256)
 scan_popc_kernel(const ScanArgs a) {
     constexpr int kProd = kEight ? 4 : 9;
@@ -172,6 +173,7 @@ scan_popc_kernel(const ScanArgs a) {
         s_tloc = kInf;
     }
     int cnt = 0;  // == s_cnt, kept uniform in registers
+    unsigned long long sum_h = 0, sum_n = 0;  // table checksum of this thread (kSum)
     for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -217,6 +219,10 @@ scan_popc_kernel(const ScanArgs a) {
                 }
                 const float s = k2_f32(r0, r1, a.k2.lf2);
                 if (a.dbg) a.dbg[((size_t)i * M + j) * M + k] = s;
+                if (kSum) {
+                    sum_h += table_hash(i, j, k, r0, r1);
+                    ++sum_n;
+                }
                 if (s <= fminf(s_tloc, s_tglob)) {
                     const int idx = atomicAdd(&s_cnt, 1);
                     cbuf[idx] = Cand{s, i, j, k};
@@ -267,6 +273,7 @@ scan_popc_kernel(const ScanArgs a) {
     __syncthreads();
     const float t = fminf(s_tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr));
     flush_cands(a, cbuf, cnt, t);
+    if (kSum) table_sum_flush(a.tsum, sum_h, sum_n);
 }
 
 }  // namespace
@@ -287,11 +294,14 @@ constexpr int kPopcSmemCap = 200 * 1024;
 template <bool kEight>
 static cudaError_t occupancy(int block, size_t smem, int* ctas_per_sm) {
     if (smem > (size_t)kPopcSmemCap) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<kEight>,
+    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<kEight, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPopcSmemCap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(scan_popc_kernel<kEight, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPopcSmemCap);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, scan_popc_kernel<kEight>,
-                                                         block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm,
+                                                         scan_popc_kernel<kEight, false>, block, smem);
 }
 
 cudaError_t scan_popc_occupancy(int block, size_t smem, int* ctas_per_sm) {
@@ -304,13 +314,15 @@ cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm) {
 
 cudaError_t launch_scan_popc(const ScanArgs& a, int grid, int block, size_t smem,
                              cudaStream_t st) {
-    scan_popc_kernel<false><<<grid, block, smem, st>>>(a);
+    if (a.tsum) scan_popc_kernel<false, true><<<grid, block, smem, st>>>(a);
+    else scan_popc_kernel<false, false><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan_popc8(const ScanArgs& a, int grid, int block, size_t smem,
                               cudaStream_t st) {
-    scan_popc_kernel<true><<<grid, block, smem, st>>>(a);
+    if (a.tsum) scan_popc_kernel<true, true><<<grid, block, smem, st>>>(a);
+    else scan_popc_kernel<true, false><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 

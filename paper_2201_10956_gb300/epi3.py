@@ -28,7 +28,7 @@ MAX_TOPK = 512
 SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_scan_pairs", "epi3_destroy",
            "epi3_last_error",
            "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
-           "epi3_scan_noalloc", "epi3_scan_scores", "epi3_batch_create", "epi3_batch_scan",
+           "epi3_scan_noalloc", "epi3_scan_scores", "epi3_scan_checksum", "epi3_batch_create", "epi3_batch_scan",
            "epi3_batch_destroy", "epi3_batch_get_stats", "epi3_batch_get_paths", "epi3_scan_batch")
 
 
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
                            ctypes.POINTER(I32)],
         "epi3_scan_noalloc": [P, P, I32, I32, I32, P, P, P],
         "epi3_scan_scores": [P, I32, P],
+        "epi3_scan_checksum": [P, I32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64)],
         "epi3_batch_create": [ctypes.POINTER(P), I32, P, I32, P],
         "epi3_batch_scan": [P, I32, P, P],
         "epi3_batch_destroy": [P],
@@ -231,6 +232,13 @@ class Handle:
         out = self._alloc((m, m, m), np.float32)
         _check(load().epi3_scan_scores(self._h, int(path), _ptr(out)))
         return out
+
+    def scan_checksum(self, path: int):
+        """(sum of table hashes mod 2^64, tables counted) of a full scan by the kernel of
+        `path`, no pruning: two counting forms agree table by table iff their sums agree."""
+        total, count = ctypes.c_uint64(0), ctypes.c_int64(0)
+        _check(load().epi3_scan_checksum(self._h, int(path), ctypes.byref(total), ctypes.byref(count)))
+        return int(total.value), int(count.value)
 
     def set_option(self, key: str, value):
         _check(load().epi3_set_option(self._h, key.encode(), str(value).encode()))

@@ -1,0 +1,93 @@
+"""Every table of a full scan, at any size (needs an sm_103 GPU): epi3_scan_checksum sums a hash
+of each counted table, so two counting forms agree table by table iff their sums agree (up to
+a 2^-64 collision).  On small inputs the sum is checked against the same hash of the oracle's
+tables; at the full workloads the tensor-core forms are checked against the 8-cell POPC form
+(itself pinned to the oracle) over all C(M, 3) tables."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import oracle_pins as pins
+from paper_2201_10956_gb300 import build as B
+import paper_2201_10956_gb300 as epi
+
+pytestmark = pytest.mark.gpu
+
+PATHS = {"popc": epi.PATH_POPC, "popc8": epi.PATH_POPC8, "mma": epi.PATH_MMA,
+         "mma16": epi.PATH_MMA16, "mma4": epi.PATH_MMA4}
+M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    return epi.load()
+
+
+def mix64(z):
+    # splitmix64 finaliser, elementwise on uint64 (arithmetic mod 2^64)
+    z = z + np.uint64(0x9E3779B97F4A7C15)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def checksum_of(trip, tab):
+    """The library's table hash (documented with epi3_scan_checksum) of [n, 3] triplets and
+    their [n, 2, 27] tables, summed mod 2^64."""
+    with np.errstate(over="ignore"):
+        t = tab.astype(np.uint64)
+        f = np.zeros(len(trip), dtype=np.uint64)
+        for q in range(27):
+            f = f * np.uint64(0x100000001B3) + t[:, 0, q] + (t[:, 1, q] << np.uint64(32))
+        tr = trip.astype(np.uint64)
+        key = (tr[:, 0] << np.uint64(42)) | (tr[:, 1] << np.uint64(21)) | tr[:, 2]
+        h = mix64(f ^ mix64(key))
+        return int(h.sum(dtype=np.uint64)), len(trip)
+
+
+@pytest.mark.parametrize("m,n,n1", [(12, 300, 140), (40, 700, 300), (33, 20000, 7000),
+                                    (9, 257, 0)])
+def test_checksum_equals_oracle_tables(m, n, n1):
+    g, ph = pins.tiny_data(m, n, n1, seed=900 + m)
+    trip = pins.all_triplets(m)
+    want = checksum_of(trip, oracle.tables(g, ph, trip))
+    with epi.Handle(g, ph) as h:
+        for name, pid in PATHS.items():
+            assert h.scan_checksum(pid) == want, name
+        h.set_option("path", "mma4")
+        for form in ("plain", "split"):
+            h.set_option("mma_form", form)
+            assert h.scan_checksum(epi.PATH_MMA4) == want, form
+        # the handle still scans normally afterwards
+        tr, sc = h.scan(5)
+    otr, osc, _ = oracle.scan_topk(g, ph, 5)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+
+
+def test_checksum_sees_one_changed_genotype():
+    g, ph = pins.tiny_data(20, 400, 200, seed=5)
+    g2 = g.copy()
+    g2[7, 123] = (g2[7, 123] + 1) % 3
+    with epi.Handle(g, ph) as h1, epi.Handle(g2, ph) as h2:
+        a, b = h1.scan_checksum(epi.PATH_MMA4), h2.scan_checksum(epi.PATH_MMA4)
+    assert a[1] == b[1] == 20 * 19 * 18 // 6 and a[0] != b[0]
+
+
+@pytest.mark.parametrize("config", ["medium", "large"])
+def test_full_size_tables_agree(config):
+    # all C(M, 3) tables of the workload: every tensor-core kind and both kernel forms against
+    # the 8-cell POPC form
+    d = gen.make_config(config)
+    m = d.genotypes.shape[0]
+    with epi.Handle(d.genotypes, d.phenotype) as h:
+        ref = h.scan_checksum(epi.PATH_POPC8)
+        assert ref[1] == m * (m - 1) * (m - 2) // 6
+        for name in ("mma4", "mma"):
+            assert h.scan_checksum(PATHS[name]) == ref, name
+        h.set_option("mma_form", "split" if config == "large" else "plain")
+        assert h.scan_checksum(epi.PATH_MMA4) == ref

@@ -118,12 +118,14 @@ def test_tensor_scan_medium_sampled(name):
 
 
 @pytest.mark.parametrize("name", ["mma", "mma4"])
-def test_bounded_wait_times_out_and_context_survives(monkeypatch, name):
+@pytest.mark.parametrize("form", ["plain", "split"])
+def test_bounded_wait_times_out_and_context_survives(monkeypatch, name, form):
     # a device wait that can only run out: the kernel must report EPI3_ERR_TIMEOUT after its
-    # 1 s limit, release its resources, and leave the context usable
+    # 1 s limit, release its resources, and leave the context usable (both kernel forms)
     g, ph = pins.tiny_data(40, 300, 120, seed=77)
     with epi.Handle(g, ph) as h:
         h.set_option("path", name)
+        h.set_option("mma_form", form)
         monkeypatch.setenv("EPI3_FAULT", "timeout")
         with pytest.raises(epi.Epi3Error) as ei:
             h.scan(5)
