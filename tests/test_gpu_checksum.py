@@ -78,7 +78,7 @@ def test_checksum_sees_one_changed_genotype():
     assert a[1] == b[1] == 20 * 19 * 18 // 6 and a[0] != b[0]
 
 
-@pytest.mark.parametrize("config", ["medium", "large"])
+@pytest.mark.parametrize("config", ["medium", "large", "stress"])
 def test_full_size_tables_agree(config):
     # all C(M, 3) tables of the workload: every tensor-core kind and both kernel forms against
     # the 8-cell POPC form
@@ -89,5 +89,5 @@ def test_full_size_tables_agree(config):
         assert ref[1] == m * (m - 1) * (m - 2) // 6
         for name in ("mma4", "mma"):
             assert h.scan_checksum(PATHS[name]) == ref, name
-        h.set_option("mma_form", "split" if config == "large" else "plain")
+        h.set_option("mma_form", "split" if config == "large" else "plain")  # the other form
         assert h.scan_checksum(epi.PATH_MMA4) == ref
