@@ -25,11 +25,13 @@
 // Shared memory: a ring of TMEM stages + 2 steps, the epilogue's candidate buffer and its
 // per-warp transpose slabs.
 //
-// Warp roles (14 warps): 0 = operand loader + TMEM allocator, 1 = MMA issuer (one wait and
-// one commit per step), 2..9 = epilogue (two warps per TMEM lane quadrant; pair-table rows,
-// TMEM read, transpose, derive27, a table-free bound that skips tables above the candidate
-// band, exact FP32 K2 for the rest), 10..13 = A producers (one thread per TMEM lane; they also
-// return each shared-memory stage to the loader once its MMAs are complete).  Every mbarrier
+// Warp roles: operand loader + TMEM allocator; MMA issuer (one wait and one commit per step);
+// 8 epilogue warps (two per TMEM lane quadrant; pair-table rows, TMEM read, transpose, the 19
+// derived cells of count + 1 in exact FP32, a table-free bound that skips tables above the
+// candidate band, the exact integer table and FP32 K2 for the rest); 4 A producers (one thread
+// per TMEM lane; they also return each shared-memory stage to the loader once its MMAs are
+// complete).  Two layouts: 14 warps with 128 registers each, or 16 warps whose groups move
+// registers to the epilogue (setmaxnreg) for data sets with fewer samples.  Every mbarrier
 // wait is bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
 // frees TMEM and returns.
 #include "epi3_internal.cuh"
