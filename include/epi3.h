@@ -176,7 +176,8 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
 int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t* out_count);
 
 /*
- * Options (strings): "path" = "auto" | "popc" | "popc8" | "mma" | "mma16" | "mma4";
+ * Options (strings): "path" = "auto" (the default: EPI3_PATH_MMA4 up to about 8700 SNPs,
+ * EPI3_PATH_POPC8 beyond) | "popc" | "popc8" | "mma" | "mma16" | "mma4";
  * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
  * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);
  * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with

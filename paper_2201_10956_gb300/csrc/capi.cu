@@ -109,7 +109,7 @@ struct epi3_handle {
     Ctrl* h_ctrl = nullptr;       // pinned
     double* h_scores = nullptr;   // pinned [EPI3_MAX_TOPK]
     int* h_trip = nullptr;        // pinned [EPI3_MAX_TOPK * 3]
-    int path = EPI3_PATH_POPC;
+    int path = EPI3_PATH_AUTO;          // scan path (option "path"); auto = E2M1 tensor form
     int threads = 128;
     int ctas_per_sm = 0;
     bool timing = false;
