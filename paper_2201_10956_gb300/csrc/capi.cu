@@ -354,10 +354,53 @@ void append_tiles(int M, long long pb, long long pe, int cohort, std::vector<int
     }
 }
 
+// The tiles of a whole scan (every pair) in append_tiles order, built on the device from one
+// {kb, jb, count, offset} entry per pair of SNP blocks: with every pair in range, each
+// i < min(j_hi, k_hi - 1) of a block pair is a tile.
+int whole_scan_tiles(epi3_handle* h) {
+    const int M = h->M;
+    const int kbc = (M + 63) / 64, jbc = (M + 31) / 32;
+    std::vector<int4> blocks;
+    long long off = 0;
+    for (int kb = 0; kb < kbc; ++kb) {
+        const int k_hi = std::min(64 * kb + 63, M - 1);
+        for (int jb = 0; jb < jbc; ++jb) {
+            const int j_lo = 32 * jb, j_hi = std::min(32 * jb + 31, M - 1);
+            if (j_lo >= k_hi) continue;
+            const int cnt = std::min(j_hi, k_hi - 1);
+            if (cnt <= 0) continue;
+            blocks.push_back(make_int4(kb, jb, cnt, (int)off));
+            off += cnt;
+        }
+    }
+    h->n_tiles = off;
+    CK(dev_alloc((void**)&h->d_tiles, sizeof(int4) * (off ? off : 1)), "alloc tiles");
+    int4* d_blocks = nullptr;
+    CK(dev_alloc((void**)&d_blocks, sizeof(int4) * (blocks.empty() ? 1 : blocks.size())),
+       "alloc tile blocks");
+    cudaError_t e = cudaSuccess;
+    if (!blocks.empty()) {
+        e = cudaMemcpyAsync(d_blocks, blocks.data(), sizeof(int4) * blocks.size(),
+                            cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_tile_list(d_blocks, (int)blocks.size(), 0, h->d_tiles, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_blocks);
+    CK(e, "tile list");
+    return EPI3_OK;
+}
+
 int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
     if (h->d_tiles && h->tiles_pb == pb && h->tiles_pe == pe) return EPI3_OK;
     cudaFree(h->d_tiles);
     h->d_tiles = nullptr;
+    if (pb == 0 && pe >= pairs(h->M)) {  // whole scan (offsets fit int: the tile list is capped)
+        const int rc = whole_scan_tiles(h);
+        if (rc != EPI3_OK) return rc;
+        h->tiles_pb = pb;
+        h->tiles_pe = pe;
+        return EPI3_OK;
+    }
     std::vector<int4> t;
     append_tiles(h->M, pb, pe, 0, t);
     h->n_tiles = (long long)t.size();

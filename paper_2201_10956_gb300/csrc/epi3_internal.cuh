@@ -125,6 +125,10 @@ size_t scan_mma_smem(int kind);
 // (two per byte).  A 128-byte operand row holds 64, 128 or 256 samples.
 enum { kKindF16 = 0, kKindE4M3 = 1, kKindE2M1 = 2 };
 int mma_samples_per_step(int kind);
+// Tensor-scan tiles of a whole scan built on the device: blocks[b] = {kb, jb, count, offset},
+// tiles (i, jb, kb, cohort) for i < count written from offset on.
+cudaError_t launch_tile_list(const int4* blocks, int n_blocks, int cohort, int4* tiles,
+                             cudaStream_t st);
 cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
                           int kb_count, int kind, cudaStream_t st);
 // One data set ("cohort") as the tensor-core scan sees it.  The kernel reads these from

@@ -1115,6 +1115,13 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
     }
 }
 
+// Tile list of a whole scan on the device: block b = {kb, jb, count, offset} of (third-SNP
+// block, second-SNP block) gets tiles (i, jb, kb, cohort) for i = 0 .. count-1 at offset + i.
+__global__ void tile_list_kernel(const int4* __restrict__ blocks, int cohort, int4* __restrict__ tiles) {
+    const int4 b = blocks[blockIdx.x];
+    for (int i = threadIdx.x; i < b.z; i += blockDim.x) tiles[b.w + i] = make_int4(i, b.y, b.x, cohort);
+}
+
 }  // namespace
 
 size_t scan_mma_smem(int kind) {
@@ -1125,6 +1132,13 @@ size_t scan_mma_smem(int kind) {
 
 int mma_samples_per_step(int kind) {
     return kind == kKindE2M1 ? 256 : (kind == kKindE4M3 ? 128 : 64);
+}
+
+cudaError_t launch_tile_list(const int4* blocks, int n_blocks, int cohort, int4* tiles,
+                             cudaStream_t st) {
+    if (n_blocks == 0) return cudaSuccess;
+    tile_list_kernel<<<n_blocks, 256, 0, st>>>(blocks, cohort, tiles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
