@@ -1130,6 +1130,12 @@ int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
     if (force && !strcmp(force, "mma")) { *path_out = EPI3_PATH_MMA4; return EPI3_OK; }
     if (force && !strcmp(force, "popc8")) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
     if (mma_tile_estimate(h->M) > kMaxMmaTiles) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
+    // A cohort whose tensor tiles cannot fill the GPU on their own is latency-bound when timed
+    // alone, yet in the batch its tiles share one persistent launch with every other cohort's
+    // (its marginal cost there is its tiles' share of that launch, at the throughput-bound
+    // rate, several times the POPC forms').  Timing it alone would be biased toward POPC, so
+    // such cohorts take the tensor form; the rest are timed on a slice that does fill the GPU.
+    if (mma_tile_estimate(h->M) < 64LL * b->sm_count) { *path_out = EPI3_PATH_MMA4; return EPI3_OK; }
     tune_load();
     const std::string dev = device_name(b->device);
     const int mb = h->M / 64, nb = h->N / 1024;

@@ -34,6 +34,8 @@
 // registers to the epilogue (setmaxnreg) for data sets with fewer samples.  Every mbarrier
 // wait is bounded; on timeout the kernel records kStTimeout, waits for its own bulk copies,
 // frees TMEM and returns.
+#include <atomic>
+
 #include "epi3_internal.cuh"
 
 namespace epi3 {
@@ -1159,15 +1161,24 @@ template <int kKind, bool kProf, bool kSplit>
 static cudaError_t launch_variant(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                                   int grid, cudaStream_t st, unsigned long long* prof) {
     const size_t smem = scan_mma_smem(kKind);
-    // the warp groups' register split adds up to exactly the launch's registers: refuse to
-    // launch a build whose register count differs (its increase could never be granted)
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, scan_mma_kernel<kKind, kProf, kSplit>);
+    // once per device: the warp groups' register split adds up to exactly the launch's
+    // registers, so refuse a build whose register count differs (its increase could never be
+    // granted); then allow the dynamic shared memory
+    static std::atomic<unsigned long long> ready{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (kSplit && fa.numRegs != kRegLaunch) return cudaErrorInvalidConfiguration;
-    e = cudaFuncSetAttribute(scan_mma_kernel<kKind, kProf, kSplit>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(ready.load(std::memory_order_acquire) & bit)) {
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, scan_mma_kernel<kKind, kProf, kSplit>);
+        if (e != cudaSuccess) return e;
+        if (kSplit && fa.numRegs != kRegLaunch) return cudaErrorInvalidConfiguration;
+        e = cudaFuncSetAttribute(scan_mma_kernel<kKind, kProf, kSplit>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ready.fetch_or(bit, std::memory_order_release);
+    }
     scan_mma_kernel<kKind, kProf, kSplit><<<grid, threads_of<kSplit>(), smem, st>>>(cohorts, tiles,
                                                                                  n_tiles, prof);
     return cudaGetLastError();
