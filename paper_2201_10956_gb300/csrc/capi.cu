@@ -394,7 +394,9 @@ int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
     if (h->d_tiles && h->tiles_pb == pb && h->tiles_pe == pe) return EPI3_OK;
     cudaFree(h->d_tiles);
     h->d_tiles = nullptr;
-    if (pb == 0 && pe >= pairs(h->M)) {  // whole scan (offsets fit int: the tile list is capped)
+    // whole scan: every pair with a third SNP after it (scan_impl clamps the range to these)
+    // (offsets fit int: the tile list is capped)
+    if (pb == 0 && pe >= pairs(h->M - 1)) {
         const int rc = whole_scan_tiles(h);
         if (rc != EPI3_OK) return rc;
         h->tiles_pb = pb;
