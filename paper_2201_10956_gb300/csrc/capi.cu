@@ -565,7 +565,8 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
         s.wait_mma_operands = (float)(p[1] / tot);
         s.wait_mma_accum = (float)(p[2] / tot);
         s.wait_producers = (float)(p[3] / (tot * 4));
-        s.wait_epilogue = (float)(p[4] / (tot * 8));
+        // the split form's eight epilogue warps each wait; the plain form's one thread waits
+        s.wait_epilogue = (float)(p[4] / (tot * (s.block == mma_threads(true) ? 8 : 1)));
         s.wait_producers_tmem = (float)(p[6] / (tot * 4));
         s.mma_issue = (float)(p[7] / tot);
     }

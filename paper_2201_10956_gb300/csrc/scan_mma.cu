@@ -906,10 +906,19 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             }
             const int M = cd.pl.M;
             const int i = tile.x, j = tile.y * kJB + jj, kb0 = tile.z * kKB;
-            bool bad = !mbar_wait_t(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag, my_acc);
-            if (bad) fail(&cd);
+            // plain form: one thread polls the accumulators' barrier and the other epilogue
+            // warps wait at the named barrier below, which costs no shared-memory traffic
+            // (there the epilogue waits for the MMA pipeline, and polling from all eight warps
+            // competes with the producers' shared-memory reads); the split form's epilogue
+            // bounds the scan, and every warp polls so that none waits for a wake-up
+            bool bad = false;
+            if (kSplit || tid == 0) {
+                bad = !mbar_wait_t(accF0 + 8 * buf, (unsigned)((tl >> 1) & 1), abort_flag, my_acc);
+                if (bad) fail(&cd);
+            }
             // uniform decision (every epilogue thread stops on the same tile); also orders the
-            // previous tile's candidate bookkeeping before this tile's appends
+            // previous tile's candidate bookkeeping before this tile's appends, and the
+            // barrier's completion, observed by thread 0, before every thread's TMEM reads
             if (epi_bar_or(bad || *abort_flag)) break;
             tc_fence_after();
             const int KS0 = cd.KS[0], KS1 = cd.KS[1];
