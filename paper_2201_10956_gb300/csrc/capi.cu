@@ -528,6 +528,9 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
         if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
         CK(cudaEventRecord(h->ev[0], h->stream), "event");
         CK(launch_reset(h->d_ctrl, h->stream), "reset launch");
+        if (h->tsum)  // a retried scan counts every table again: the checksum restarts with it
+            CK(cudaMemsetAsync(h->tsum, 0, 2 * kTsumSlots * sizeof(unsigned long long), h->stream),
+               "clear checksum slots");
         CK(cudaEventRecord(h->ev[1], h->stream), "event");
         const CohortDev cd = cohort_of(h, pb, pe, top_k);
         CK(cudaMemcpyAsync(h->d_cd, &cd, sizeof(cd), cudaMemcpyHostToDevice, h->stream),
@@ -624,6 +627,9 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
         CK(cudaEventRecord(h->ev[0], h->stream), "event");
         CK(launch_reset(h->d_ctrl, h->stream), "reset launch");
+        if (h->tsum)  // a retried scan counts every table again: the checksum restarts with it
+            CK(cudaMemsetAsync(h->tsum, 0, 2 * kTsumSlots * sizeof(unsigned long long), h->stream),
+               "clear checksum slots");
         ScanArgs a;
         a.pl = h->pl;
         a.k2 = h->k2;
