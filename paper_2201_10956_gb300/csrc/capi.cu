@@ -42,7 +42,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 // Fault injection for tests of the error paths, all without faulting the GPU:
 // EPI3_FAULT=alloc makes device allocations fail, EPI3_FAULT=launch makes scan launches fail,
 // EPI3_FAULT=timeout makes the tensor-core scan's MMA issuer wait on a barrier nobody
-// signals, so its bounded wait runs out (1 s) and the scan returns EPI3_ERR_TIMEOUT.
+// signals, so its bounded wait runs out (1 s) and the scan returns EPI3_ERR_TIMEOUT;
+// EPI3_FAULT=cand starts a handle with a 128-entry candidate list, so scans overflow it and
+// take the retry path with a larger list.
 bool inject(const char* what) {
     const char* f = getenv("EPI3_FAULT");
     return f && strcmp(f, what) == 0;
@@ -288,7 +290,7 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     cleanup();
     if (rc != EPI3_OK) return rc;
     if ((rc = build_k2_tables(h)) != EPI3_OK) return rc;
-    h->cand_cap = 1LL << 16;
+    h->cand_cap = inject("cand") ? 128 : 1LL << 16;
     CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "alloc candidates");
     CK(dev_alloc((void**)&h->d_fin, sizeof(Final) * kFinalCap), "alloc final");
     CK(dev_alloc((void**)&h->d_out_scores, sizeof(double) * EPI3_MAX_TOPK), "alloc out scores");

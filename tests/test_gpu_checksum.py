@@ -91,3 +91,19 @@ def test_full_size_tables_agree(config):
             assert h.scan_checksum(PATHS[name]) == ref, name
         h.set_option("mma_form", "split" if config == "large" else "plain")  # the other form
         assert h.scan_checksum(epi.PATH_MMA4) == ref
+
+
+@pytest.mark.parametrize("name", ["popc8", "mma4"])
+def test_retried_scan_restarts_the_checksum(monkeypatch, name):
+    # a 128-entry candidate list overflows, so the scan is retried with a larger one; the
+    # retry counts every table again and the checksum must count it once
+    g, ph = pins.tiny_data(90, 1500, 700, seed=17)
+    trip = pins.all_triplets(90)
+    want = checksum_of(trip, oracle.tables(g, ph, trip))
+    monkeypatch.setenv("EPI3_FAULT", "cand")
+    with epi.Handle(g, ph) as h:
+        assert h.scan_checksum(PATHS[name]) == want
+        h.set_option("path", name)
+        tr, sc = h.scan(20)
+    otr, osc, _ = oracle.scan_topk(g, ph, 20)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
