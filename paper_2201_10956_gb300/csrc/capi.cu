@@ -95,6 +95,8 @@ struct epi3_handle {
     void* d_pair_scratch = nullptr;  // pairwise scan: selection passes + outputs
     size_t pair_scratch_bytes = 0;
     int2* d_marg = nullptr;
+    float4* d_ptf = nullptr;         // tensor scan: pair tables + 3 as FP32
+    float2* d_margf = nullptr;       // tensor scan: marginals + 9 as FP32
     PairTables ptab{};
     uint8_t* d_oh = nullptr;      // pre-tiled one-hot operand of the tensor-core form
     int oh_kind = -1;             // element kind d_oh was built for (kKind*, -1: none)
@@ -135,6 +137,8 @@ void release(epi3_handle* h) {
     cudaFree(h->d_pt);
     cudaFree(h->d_pair_scratch);
     cudaFree(h->d_marg);
+    cudaFree(h->d_ptf);
+    cudaFree(h->d_margf);
     cudaFree(h->d_oh);
     cudaFree(h->d_tiles);
     cudaFree(h->d_cd);
@@ -318,6 +322,15 @@ int ensure_pair_tables(epi3_handle* h) {
 
 // Tensor-core form: pre-tiled one-hot operand (built once per element type).
 int ensure_onehot(epi3_handle* h, int kind) {
+    if (!h->d_ptf) {  // the tensor scan's FP32 copies of the pair tables (built once)
+        const long long np = h->ptab.n_pairs;
+        CK(dev_alloc((void**)&h->d_ptf, sizeof(float4) * 2 * (size_t)np), "alloc FP32 pair tables");
+        CK(dev_alloc((void**)&h->d_margf, sizeof(float2) * 2 * (size_t)h->M), "alloc FP32 marginals");
+        CK(launch_pair_floats(h->d_pt, h->d_marg, np, h->M, h->d_ptf, h->d_margf, h->stream),
+           "FP32 pair tables launch");
+        h->ptab.ptf = h->d_ptf;
+        h->ptab.margf = h->d_margf;
+    }
     if (h->d_oh && h->oh_kind == kind) return EPI3_OK;
     cudaFree(h->d_oh);
     h->d_oh = nullptr;

@@ -77,6 +77,10 @@ struct PairTables {
     const int2* marg;
     long long n_pairs;
     int n_c[2];
+    // the tensor scan's copies in FP32 (exact), offset for its count + 1 arithmetic: every
+    // pair-table entry + 3, every marginal + 9 (null until that scan needs them)
+    const float4* ptf;
+    const float2* margf;
 };
 
 struct ScanArgs {
@@ -118,6 +122,9 @@ cudaError_t launch_pair_scan(const PairTables& pt, const double* lf64, int M, in
 cudaError_t launch_approx_error(const double* lf64, int n_lf, double* out, cudaStream_t st);
 cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long n_pairs,
                                cudaStream_t st);
+// ptf = pt + 3 and margf = marg + 9 as FP32 (2 n_pairs and 2 M entries)
+cudaError_t launch_pair_floats(const int4* pt, const int2* marg, long long n_pairs, int M,
+                               float4* ptf, float2* margf, cudaStream_t st);
 cudaError_t launch_scan_popc8(const ScanArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 size_t scan_popc8_smem(const Planes& pl);
 size_t scan_mma_smem(int kind);

@@ -49,7 +49,30 @@ pair_tables_kernel(Planes pl, int4* __restrict__ pt, int2* __restrict__ marg, lo
     }
 }
 
+__global__ void pair_floats_kernel(const int4* __restrict__ pt, const int2* __restrict__ marg,
+                                   long long n_pt, long long n_marg, float4* __restrict__ ptf,
+                                   float2* __restrict__ margf) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_pt + n_marg;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < n_pt) {
+            const int4 q = pt[t];
+            ptf[t] = make_float4((float)(q.x + 3), (float)(q.y + 3), (float)(q.z + 3), (float)(q.w + 3));
+        } else {
+            const int2 q = marg[t - n_pt];
+            margf[t - n_pt] = make_float2((float)(q.x + 9), (float)(q.y + 9));
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pair_floats(const int4* pt, const int2* marg, long long n_pairs, int M,
+                               float4* ptf, float2* margf, cudaStream_t st) {
+    const long long n = 2 * n_pairs + 2LL * M;
+    const int blocks = (int)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8);
+    pair_floats_kernel<<<blocks, 256, 0, st>>>(pt, marg, 2 * n_pairs, 2LL * M, ptf, margf);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long n_pairs,
                                cudaStream_t st) {

@@ -371,17 +371,16 @@ __device__ __forceinline__ RowCells row_cells(int4 pxy, int2 mx, int2 my, int nc
 }
 
 // u[9 gX + 3 gY + gZ] = cell count + 1 of one class, from the 8 accumulated cells
-// n8[4a + 2b + z] (already + 1) and the pair tables (X, Z), (Y, Z) and marginal of Z:
-// the inclusion-exclusion of derive27 with every term shifted by one.
-__device__ __forceinline__ void cells_u(const float* n8, const RowCells& rc, int4 pxz, int4 pyz,
-                                        int2 mz, float* u) {
-    const float xz[2][2] = {{count_plus(pxz.x, 3.f), count_plus(pxz.y, 3.f)},
-                            {count_plus(pxz.z, 3.f), count_plus(pxz.w, 3.f)}};
-    const float yz[2][2] = {{count_plus(pyz.x, 3.f), count_plus(pyz.y, 3.f)},
-                            {count_plus(pyz.z, 3.f), count_plus(pyz.w, 3.f)}};
+// n8[4a + 2b + z] (already + 1) and the FP32 copies of the pair tables (X, Z), (Y, Z) (each
+// entry + 3) and of the marginal of Z (+ 9): the inclusion-exclusion of derive27 with every
+// term shifted by one.
+__device__ __forceinline__ void cells_u(const float* n8, const RowCells& rc, float4 pxz, float4 pyz,
+                                        float2 mz9, float* u) {
+    const float xz[2][2] = {{pxz.x, pxz.y}, {pxz.z, pxz.w}};
+    const float yz[2][2] = {{pyz.x, pyz.y}, {pyz.z, pyz.w}};
     // #(X = 2, Z = z) + 3 = (#(Z = z) + 9) - (#(X=0, Z=z) + 3) - (#(X=1, Z=z) + 3)
-    const float z2[2] = {__fsub_rn(__fsub_rn(count_plus(mz.x, 9.f), xz[0][0]), xz[1][0]),
-                         __fsub_rn(__fsub_rn(count_plus(mz.y, 9.f), xz[0][1]), xz[1][1])};
+    const float z2[2] = {__fsub_rn(__fsub_rn(mz9.x, xz[0][0]), xz[1][0]),
+                         __fsub_rn(__fsub_rn(mz9.y, xz[0][1]), xz[1][1])};
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -958,8 +957,8 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 // this lane's two triplets (k = kb0 + 8 g + 2 me + m): their pair-table rows
                 // are requested first, so the loads overlap the TMEM read and the transpose
                 // (an index outside the triangle reads entry 0 and is not used)
-                int4 tik[2][2], tjk[2][2];
-                int2 tmk[2][2];
+                float4 tik[2][2], tjk[2][2];
+                float2 tmk[2][2];
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     const int k = kb0 + 8 * g + 2 * me + m;
@@ -968,9 +967,9 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     const int kq = val ? k : 0;
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        tik[m][c] = __ldg(pt.pt + c * pt.n_pairs + pik);
-                        tjk[m][c] = __ldg(pt.pt + c * pt.n_pairs + pjk);
-                        tmk[m][c] = __ldg(pt.marg + (size_t)c * M + kq);
+                        tik[m][c] = __ldg(pt.ptf + c * pt.n_pairs + pik);
+                        tjk[m][c] = __ldg(pt.ptf + c * pt.n_pairs + pjk);
+                        tmk[m][c] = __ldg(pt.margf + (size_t)c * M + kq);
                     }
                 }
                 uint32_t v[2][16];
