@@ -165,7 +165,8 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
  * Debug / test: an order-independent checksum of every table that the scan kernel of `path`
  * (EPI3_PATH_*) counts in a full scan of the handle's data set (no pruning), so two counting
  * forms can be compared table by table at any size.  Each triplet i < j < k with class
- * tables r0[27], r1[27] (cell 9 gX + 3 gY + gZ) contributes
+ * tables r0[27], r1[27] (the controls' and cases' frequency tables of Eq. 1, Sec. III; cell
+ * 9 gX + 3 gY + gZ) contributes
  *     f = fold over q = 0..26 of  f * 0x100000001B3 + r0[q] + (r1[q] << 32)   (from f = 0),
  *     hash = mix(f XOR mix((i << 42) | (j << 21) | k)),
  * mix the splitmix64 finaliser (add 0x9E3779B97F4A7C15; xor-shift 30, multiply
