@@ -225,11 +225,12 @@ int epi3_get_stats(const epi3_handle* h, epi3_stats* out);
 /*
  * The whole scan (epi3_create + epi3_scan + epi3_destroy) without allocating memory.
  * The paper has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running while a CUDA graph is being captured, hosts with a fixed
- * memory budget, or frameworks whose own caching allocator owns the device memory (a raw
- * cudaMalloc/cudaFree there may fail or implicitly synchronise the device).
+ * cudaMalloc -- hosts with a fixed memory budget, or frameworks whose own caching
+ * allocator owns the device memory (a raw cudaMalloc/cudaFree there may fail or
+ * implicitly synchronise the device).
  *
- *   genotypes, phenotype   device pointers, same layout and values as epi3_create.
+ *   genotypes, phenotype   device pointers, same layout and values as epi3_create
+ *                          (a genotype > 2 or phenotype > 1 gives EPI3_ERR_ARG).
  *   n_snps, n_samples      M >= 3, 1 <= N <= 65536, and the packed planes, tables and
  *                          candidate lists must fit EPI3_NOALLOC_SCRATCH_BYTES (8 MiB:
  *                          about M * N <= 2.5e7, e.g. 1024 x 20000); larger sizes are
@@ -237,14 +238,20 @@ int epi3_get_stats(const epi3_handle* h, epi3_stats* out);
  *   top_k, out_triplets, out_scores   as epi3_scan, but the outputs are device pointers.
  *   cuda_stream            stream to run on (NULL = the legacy default stream).
  *
+ * It counts with the 27-cell POPC scan (EPI3_PATH_POPC, about 5 T sample-triplets/s on
+ * GB300), not the tensor-core form epi3_scan uses by default, and its candidate list has a
+ * fixed 65536 entries with no retry: a data set with more near-tied FP32 candidates gives
+ * EPI3_ERR_OVERFLOW where epi3_scan would grow the list.  The answer is the one epi3_scan
+ * gives.
+ *
  * All scratch lives in one file-scope __device__ array of EPI3_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library holds until the process exits.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress) with the device current, so
- * make the first call on each device before any stream capture.  Calls share the array and
- * it keeps the last call's contents; each call re-initialises what it reads.  Calls are
- * serialised on the host and return when the results are written; calls that overlap on
- * the GPU would race on the array.  The candidate list cannot grow: a data set with more
- * near-tied FP32 candidates than it holds gives EPI3_ERR_OVERFLOW (use epi3_scan).
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current.
+ * Calls share the array and it keeps the last call's contents; each call re-initialises
+ * what it reads.  Calls are serialised on the host; each reads status words back and
+ * synchronises the stream, so the call cannot be recorded into a CUDA graph (do not call it
+ * on a capturing stream) and returns when the results are written.  Calls that overlap on
+ * the GPU (e.g. from several processes sharing one context) would race on the array.
  */
 #define EPI3_NOALLOC_SCRATCH_BYTES (8u << 20)
 int epi3_scan_noalloc(const uint8_t* genotypes, const uint8_t* phenotype, int32_t n_snps,

@@ -1,13 +1,20 @@
 // epi3_scan_noalloc: the whole scan without allocating any memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
-// captured, real-time or embedded hosts with a fixed memory budget, and frameworks whose
-// caching allocator owns the device memory (a raw cudaMalloc/cudaFree there can fail or
-// implicitly synchronise the device).  For them this entry point runs the same kernels as
-// epi3_create + epi3_scan, but every piece of scratch memory (class permutation, packed
-// bit planes, log-factorial tables, control block, candidate lists) lives in one
-// file-scope device array of kScratchBytes, and the log-factorial tables are staged in
-// file-scope host arrays.  The caller passes device inputs and device outputs.
+// Some callers cannot call cudaMalloc: real-time or embedded hosts with a fixed memory
+// budget, and frameworks whose caching allocator owns the device memory (a raw
+// cudaMalloc/cudaFree there can fail or implicitly synchronise the device).  For them this
+// entry point runs the class split, the packing, the 27-cell POPC scan (the counting kernel
+// of the popc path, about 5 T sample-triplets/s on GB300; not the tensor-core form that
+// epi3_scan picks by default), the candidate band, FP64 rescoring and the final order, with
+// every piece of scratch memory (class permutation, packed bit planes, log-factorial
+// tables, control block, candidate lists) in one file-scope device array of kScratchBytes;
+// the log-factorial tables are staged in file-scope host arrays.  The caller passes device
+// inputs and device outputs.  The candidate list has a fixed 65536 entries and is not
+// grown: a data set with more FP32 candidates gets EPI3_ERR_OVERFLOW (epi3_scan would retry
+// with a larger list).
+//
+// The call reads status words back and synchronises its stream twice, so it cannot be
+// recorded into a CUDA graph: do not call it on a capturing stream.
 //
 // The array belongs to the library image: every GPU that loads the library holds its
 // kScratchBytes until the process exits.  All calls share it and it keeps the previous
@@ -139,6 +146,11 @@ int scan_noalloc(const uint8_t* geno, const uint8_t* pheno, int M, int N, int to
     pl.pad[0] = kSamplesPerGroup * pl.W4[0] - hc[0];
     pl.pad[1] = kSamplesPerGroup * pl.W4[1] - hc[1];
     NA_CK(launch_pack(geno, M, N, perm, hc[0], hc[1], pl, planes, ctrl, st), "pack launch");
+    // the pack kernel flags genotype values > 2 in the control block, which the reset before
+    // the scan clears: read it now
+    NA_CK(cudaMemcpyAsync(&hctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read status");
+    NA_CK(cudaStreamSynchronize(st), "pack");
+    if (hctrl.status & kStBadGenotype) return err(EPI3_ERR_ARG, "genotype value > 2");
 
     // log-factorial tables of Eq. 1: the same recurrence and split as epi3_create
     h_lf64[0] = 0.0;
@@ -183,7 +195,6 @@ int scan_noalloc(const uint8_t* geno, const uint8_t* pheno, int M, int N, int to
     NA_CK(launch_final(ctrl, fin, top_k, out_scores, out_trip, st), "final launch");
     NA_CK(cudaMemcpyAsync(&hctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read status");
     NA_CK(cudaStreamSynchronize(st), "scan");
-    if (hctrl.status & kStBadGenotype) return err(EPI3_ERR_ARG, "genotype value > 2");
     if (hctrl.status & kStCandOverflow)
         return err(EPI3_ERR_OVERFLOW, "more FP32 candidates than the static candidate list holds");
     if (hctrl.status & kStFinalOverflow)

@@ -346,10 +346,10 @@ def scan_batch(datasets, top_k: int):
 def scan_noalloc(genotypes, phenotype, top_k: int, stream=None):
     """epi3_scan_noalloc on CUDA tensors: the scan with no memory allocated by the library.
 
-    For callers that cannot allocate (graph capture, fixed memory budgets, foreign
-    allocators); the outputs are allocated here by torch, the scratch is the library's
-    static device array (8 MiB).  Returns (triplets int32 [k, 3], scores float64 [k]) on
-    the device.
+    For callers that cannot allocate (fixed memory budgets, foreign allocators); the
+    outputs are allocated here by torch, the scratch is the library's static device array
+    (8 MiB).  It runs the 27-cell POPC scan and synchronises the stream, so it is not for
+    a capturing stream.  Returns (triplets int32 [k, 3], scores float64 [k]) on the device.
     """
     import torch
     m, n = genotypes.shape

@@ -1,12 +1,12 @@
 """epi3_scan_noalloc: the scan for callers that cannot allocate device memory.
 
-Such callers (code inside CUDA-graph capture, fixed-budget hosts, frameworks whose own
-allocator owns the GPU) get the whole scan with its scratch in the library's static
-device array.  These tests call the entry point through the C ABI and check that its
-answer equals the allocating path's (epi3_create + epi3_scan): identical triplets and
-bit-identical FP64 scores, on two calls in a row with different data sets, so the
-second call also shows that stale contents of the shared array do not leak.  This file
-is collected last on purpose.
+Such callers (fixed-budget hosts, frameworks whose own allocator owns the GPU) get the
+whole scan with its scratch in the library's static device array.  These tests call the
+entry point through the C ABI and check that its answer equals the CPU oracle's and the
+allocating path's (epi3_create + epi3_scan): identical triplets and bit-identical FP64
+scores, on two calls in a row with different data sets, so the second call also shows
+that stale contents of the shared array do not leak.  Bad genotype and phenotype values
+must be refused.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 import oracle_pins as pins
 from paper_2201_10956_gb300 import build as B
 import paper_2201_10956_gb300 as epi
@@ -30,7 +31,7 @@ def lib():
     return epi.load()
 
 
-def noalloc_scan(lib, g, ph, k):
+def noalloc_call(lib, g, ph, k):
     import torch
     gd = torch.from_numpy(np.ascontiguousarray(g)).cuda()
     pd = torch.from_numpy(np.ascontiguousarray(ph)).cuda()
@@ -41,8 +42,13 @@ def noalloc_scan(lib, g, ph, k):
     rc = lib.epi3_scan_noalloc(ctypes.c_void_p(gd.data_ptr()), ctypes.c_void_p(pd.data_ptr()),
                                g.shape[0], g.shape[1], k, ctypes.c_void_p(trip.data_ptr()),
                                ctypes.c_void_p(sc.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    return rc, trip.cpu().numpy(), sc.cpu().numpy()
+
+
+def noalloc_scan(lib, g, ph, k):
+    rc, trip, sc = noalloc_call(lib, g, ph, k)
     assert rc == epi.OK, epi.last_error()
-    return trip.cpu().numpy(), sc.cpu().numpy()
+    return trip, sc
 
 
 def allocating_scan(g, ph, k):
@@ -55,9 +61,28 @@ def test_noalloc_matches_allocating_scan_twice(lib):
     g2, ph2 = pins.tiny_data(200, 1000, 421, seed=77)       # ragged class sizes
     for g, ph, k in ((d1.genotypes, d1.phenotype, 10), (g2, ph2, 25)):
         tr, sc = noalloc_scan(lib, g, ph, k)
+        otr, osc, _ = oracle.scan_topk(g, ph, k)
+        assert np.array_equal(tr, otr), (tr[:3], otr[:3])
+        assert np.array_equal(sc, osc)
         rtr, rsc = allocating_scan(g, ph, k)
         assert np.array_equal(tr, rtr), (tr[:3], rtr[:3])
         assert np.array_equal(sc, rsc)
+
+
+def test_noalloc_refuses_bad_values(lib):
+    g, ph = pins.tiny_data(20, 300, 150, seed=5)
+    bad = g.copy()
+    bad[7, 123] = 3                                         # genotype outside 0..2
+    rc, _, _ = noalloc_call(lib, bad, ph, 5)
+    assert rc == epi.ERR_ARG and "genotype" in epi.last_error()
+    badp = ph.copy()
+    badp[17] = 2                                            # phenotype outside 0..1
+    rc, _, _ = noalloc_call(lib, g, badp, 5)
+    assert rc == epi.ERR_ARG and "phenotype" in epi.last_error()
+    # the array is usable again right after a refused call
+    tr, sc = noalloc_scan(lib, g, ph, 5)
+    otr, osc, _ = oracle.scan_topk(g, ph, 5)
+    assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_array(lib):
