@@ -78,6 +78,9 @@ def test_batch_device_inputs():
 
 @pytest.mark.slow
 def test_batch_config_48_cohorts():
+    # the 48-cohort workload: per cohort the oracle rescores the answer exactly, and no triplet
+    # of an oracle-scored sample (1e5 random triplets plus every triplet containing the first
+    # SNP of the planted triplet) outside the answer scores below its 5th
     cohorts = gen.make_batch(seed=1)
     data = [(d.genotypes, d.phenotype) for d in cohorts]
     with epi.Batch(data) as b:
@@ -85,9 +88,28 @@ def test_batch_config_48_cohorts():
         paths = b.paths()
     assert set(paths.tolist()) <= {epi.PATH_MMA4, epi.PATH_POPC8}
     for c, d in enumerate(cohorts):
-        # the oracle rescores the answer exactly, and the single-handle scan agrees
-        assert np.array_equal(oracle.scores(d.genotypes, d.phenotype, tr[c]), sc[c])
+        g, ph = d.genotypes, d.phenotype
+        assert np.array_equal(oracle.scores(g, ph, tr[c]), sc[c])
         assert np.all(np.diff(sc[c]) >= 0)
-        with epi.Handle(d.genotypes, d.phenotype) as h:
+        assert np.all(tr[c][:, 0] < tr[c][:, 1]) and np.all(tr[c][:, 1] < tr[c][:, 2])
+        samp = np.concatenate([gen.random_triplets(d.n_snps, 100_000, seed=c),
+                               triplets_with(d.n_snps, int(d.planted[0][0]))])
+        ref = oracle.scores(g, ph, samp)
+        got = {tuple(t) for t in tr[c]}
+        for t in samp[ref < sc[c][-1]]:
+            assert tuple(t) in got, (c, t)
+        # ties with the 5th score are broken by (i, j, k): none of the sample may precede it
+        last = tuple(tr[c][-1])
+        for t in samp[ref == sc[c][-1]]:
+            assert tuple(t) in got or tuple(t) > last, (c, t)
+        with epi.Handle(g, ph) as h:
             htr, hsc = h.scan(5)
         assert np.array_equal(htr, tr[c]) and np.array_equal(hsc, sc[c])
+
+
+def triplets_with(m, p):
+    """Every triplet i<j<k of m SNPs that contains SNP p."""
+    rest = np.array([x for x in range(m) if x != p], dtype=np.int32)
+    a, b = np.triu_indices(m - 1, 1)
+    t = np.stack([rest[a], rest[b], np.full(a.size, p, dtype=np.int32)], axis=1)
+    return np.sort(t, axis=1).astype(np.int32)
