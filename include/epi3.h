@@ -199,7 +199,7 @@ typedef struct {
     float scan_kernel_ms;    /* counting + FP32 scoring kernel (timing = 1) */
     float select_ms;         /* threshold selection + FP64 rescoring + final sort */
     float total_ms;          /* whole scan, device time (timing = 1) */
-    float pack_ms;           /* class split + bit-plane packing at create (timing = 1) */
+    float pack_ms;           /* bit-plane packing at create: plane zeroing + pack kernel */
     int32_t path;            /* EPI3_PATH_* used */
     int32_t grid;            /* CTAs launched by the scan kernel */
     int32_t block;           /* threads per CTA */

@@ -237,7 +237,6 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     const size_t MN = (size_t)h->M * h->N;
     uint8_t* d_geno = nullptr;
     uint8_t* d_pheno = nullptr;
-    int* d_perm = nullptr;
     int* d_counts = nullptr;
     int rc = EPI3_OK;
     auto cleanup = [&]() {
@@ -245,7 +244,6 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
             cudaFree(d_geno);
             cudaFree(d_pheno);
         }
-        cudaFree(d_perm);
         cudaFree(d_counts);
     };
     do {
@@ -261,11 +259,9 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
             if ((e = cudaMemcpyAsync(d_geno, geno, MN, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "copy genotypes"); break; }
             if ((e = cudaMemcpyAsync(d_pheno, pheno, h->N, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "copy phenotype"); break; }
         }
-        if ((e = dev_alloc((void**)&d_perm, sizeof(int) * h->N)) != cudaSuccess) { rc = cuda_fail(e, "alloc perm"); break; }
-        if ((e = dev_alloc((void**)&d_counts, sizeof(int) * 2)) != cudaSuccess) { rc = cuda_fail(e, "alloc counts"); break; }
-        if ((e = cudaEventRecord(h->ev[0], h->stream)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+        if ((e = dev_alloc((void**)&d_counts, sizeof(int) * class_counts_len(h->N))) != cudaSuccess) { rc = cuda_fail(e, "alloc counts"); break; }
         if ((e = launch_reset(h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "reset"); break; }
-        if ((e = launch_class_index(d_pheno, h->N, d_perm, d_counts, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index launch"); break; }
+        if ((e = launch_class_index(d_pheno, h->N, d_counts, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index launch"); break; }
         int counts[2] = {0, 0};
         if ((e = cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read counts"); break; }
         if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
@@ -284,7 +280,8 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
         const size_t n4 = 2ull * (pl.W4[0] + pl.W4[1]) * h->M;
         if ((e = dev_alloc((void**)&h->d_planes, n4 * sizeof(uint4))) != cudaSuccess) { rc = cuda_fail(e, "alloc planes"); break; }
         pl.planes = h->d_planes;
-        if ((e = launch_pack(d_geno, h->M, h->N, d_perm, h->N0, h->N1, pl, h->d_planes, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "pack launch"); break; }
+        if ((e = cudaEventRecord(h->ev[0], h->stream)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+        if ((e = launch_pack(d_geno, d_pheno, h->M, h->N, d_counts, h->N0, h->N1, pl, h->d_planes, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "pack launch"); break; }
         if ((e = cudaEventRecord(h->ev[1], h->stream)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
         if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
         if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "pack"); break; }

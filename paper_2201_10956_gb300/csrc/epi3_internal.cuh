@@ -97,10 +97,14 @@ struct ScanArgs {
 };
 
 // launchers (return cudaError_t of the launch)
-cudaError_t launch_class_index(const uint8_t* pheno, int N, int* perm, int* counts, Ctrl* ctrl,
+// counts[0] = controls, counts[1] = cases, counts[2 + q] = cases before sample 1024 q
+// (class_counts_len(N) ints); the pack kernel reads them to place each chunk's samples.
+size_t class_counts_len(int N);
+cudaError_t launch_class_index(const uint8_t* pheno, int N, int* counts, Ctrl* ctrl,
                                cudaStream_t st);
-cudaError_t launch_pack(const uint8_t* geno, int M, int N, const int* perm, int N0, int N1,
-                        const Planes& pl, uint4* planes, Ctrl* ctrl, cudaStream_t st);
+// zeroes the planes, then packs (both on st)
+cudaError_t launch_pack(const uint8_t* geno, const uint8_t* pheno, int M, int N, const int* counts,
+                        int N0, int N1, const Planes& pl, uint4* planes, Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_scan_popc(const ScanArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 size_t scan_popc_smem(const Planes& pl);
 cudaError_t scan_popc_occupancy(int block, size_t smem, int* ctas_per_sm);

@@ -6,8 +6,8 @@
 // entry point runs the class split, the packing, the 27-cell POPC scan (the counting kernel
 // of the popc path, about 5 T sample-triplets/s on GB300; not the tensor-core form that
 // epi3_scan picks by default), the candidate band, FP64 rescoring and the final order, with
-// every piece of scratch memory (class permutation, packed bit planes, log-factorial
-// tables, control block, candidate lists) in one file-scope device array of kScratchBytes;
+// every piece of scratch memory (class counts, packed bit planes, log-factorial tables,
+// control block, candidate lists) in one file-scope device array of kScratchBytes;
 // the log-factorial tables are staged in file-scope host arrays.  The caller passes device
 // inputs and device outputs.  The candidate list has a fixed 65536 entries and is not
 // grown: a data set with more FP32 candidates gets EPI3_ERR_OVERFLOW (epi3_scan would retry
@@ -58,7 +58,7 @@ int err(int code, const char* msg, cudaError_t e = cudaSuccess) {
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t ctrl, counts, perm, planes, lf2, lf64, cand, fin, total;
+    size_t ctrl, counts, planes, lf2, lf64, cand, fin, total;
 };
 
 // Offsets inside the scratch array; the planes are sized for the worst class split.
@@ -66,8 +66,7 @@ Layout layout(long long M, long long N) {
     Layout L{};
     size_t o = 0;
     L.ctrl = o;   o += up256(sizeof(Ctrl));
-    L.counts = o; o += up256(2 * sizeof(int));
-    L.perm = o;   o += up256((size_t)N * sizeof(int));
+    L.counts = o; o += up256(class_counts_len((int)N) * sizeof(int));
     const long long groups = (N + kSamplesPerGroup - 1) / kSamplesPerGroup + 1;
     L.planes = o; o += up256((size_t)2 * groups * M * sizeof(uint4));
     L.lf2 = o;    o += up256((size_t)(N + 2) * sizeof(float2));
@@ -119,7 +118,6 @@ int scan_noalloc(const uint8_t* geno, const uint8_t* pheno, int M, int N, int to
     unsigned char* base = static_cast<unsigned char*>(g_dev_scratch[dev]);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + L.ctrl);
     int* counts = reinterpret_cast<int*>(base + L.counts);
-    int* perm = reinterpret_cast<int*>(base + L.perm);
     uint4* planes = reinterpret_cast<uint4*>(base + L.planes);
     float2* lf2 = reinterpret_cast<float2*>(base + L.lf2);
     double* lf64 = reinterpret_cast<double*>(base + L.lf64);
@@ -128,7 +126,7 @@ int scan_noalloc(const uint8_t* geno, const uint8_t* pheno, int M, int N, int to
 
     // class split
     NA_CK(launch_reset(ctrl, st), "reset launch");
-    NA_CK(launch_class_index(pheno, N, perm, counts, ctrl, st), "class_index launch");
+    NA_CK(launch_class_index(pheno, N, counts, ctrl, st), "class_index launch");
     int hc[2] = {0, 0};
     Ctrl hctrl;
     NA_CK(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st), "read counts");
@@ -145,7 +143,7 @@ int scan_noalloc(const uint8_t* geno, const uint8_t* pheno, int M, int N, int to
     pl.coff[1] = 2LL * pl.W4[0] * M;
     pl.pad[0] = kSamplesPerGroup * pl.W4[0] - hc[0];
     pl.pad[1] = kSamplesPerGroup * pl.W4[1] - hc[1];
-    NA_CK(launch_pack(geno, M, N, perm, hc[0], hc[1], pl, planes, ctrl, st), "pack launch");
+    NA_CK(launch_pack(geno, pheno, M, N, counts, hc[0], hc[1], pl, planes, ctrl, st), "pack launch");
     // the pack kernel flags genotype values > 2 in the control block, which the reset before
     // the scan clears: read it now
     NA_CK(cudaMemcpyAsync(&hctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read status");
