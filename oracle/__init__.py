@@ -58,6 +58,13 @@ class Oracle:
         lib.oracle_pair_tables.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, P, P]
         lib.oracle_scan_pairs_topk.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                                P, P, ctypes.c_int32]
+        lib.oracle_tables_order.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int64, P, P]
+        lib.oracle_k2_cells.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P]
+        lib.oracle_scan_order_topk.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                               ctypes.c_int32, P, P, ctypes.c_int32]
+        for f in (lib.oracle_tables_order, lib.oracle_k2_cells, lib.oracle_scan_order_topk):
+            f.restype = ctypes.c_int
         for f in (lib.oracle_log_factorials, lib.oracle_tables, lib.oracle_k2, lib.oracle_scores,
                   lib.oracle_scan_topk):
             f.restype = ctypes.c_int
@@ -132,6 +139,43 @@ class Oracle:
         return pairs, sc, rc
 
 
+    def tables_order(self, genotypes, phenotype, snps) -> np.ndarray:
+        """[n, 2, 3^order] int32 tables of SNP sets snps [n, order] (Eq. 1 for `order` SNPs;
+        cell = genotypes as base-3 digits, first SNP most significant)."""
+        g, p = _inputs(genotypes, phenotype)
+        x = np.ascontiguousarray(snps, dtype=np.int32)
+        if x.ndim != 2:
+            raise ValueError("snps must be [n, order]")
+        order = x.shape[1]
+        out = np.empty((x.shape[0], 2, 3 ** order), dtype=np.int32)
+        if self._lib.oracle_tables_order(_ptr(g), _ptr(p), g.shape[0], g.shape[1], order,
+                                         x.shape[0], _ptr(x), _ptr(out)):
+            raise ValueError("bad order, SNP index or genotype/phenotype value")
+        return out
+
+    def k2_cells(self, tables_) -> np.ndarray:
+        """FP64 K2 (Eq. 1) of [n, 2, ncell] tables, summed in cell order."""
+        t = np.ascontiguousarray(tables_, dtype=np.int32)
+        if t.ndim != 3 or t.shape[1] != 2:
+            raise ValueError("tables must be [n, 2, ncell]")
+        out = np.empty(t.shape[0], dtype=np.float64)
+        if self._lib.oracle_k2_cells(t.shape[0], t.shape[2], _ptr(t), _ptr(out)):
+            raise ValueError("negative count")
+        return out
+
+    def scan_order_topk(self, genotypes, phenotype, order: int, top_k: int, threads: int = 0):
+        """Exhaustive scan over every set of `order` SNPs; returns (sets int32 [k, order],
+        K2 float64 [k], threads used), ordered by (K2, SNP indices)."""
+        g, p = _inputs(genotypes, phenotype)
+        x = np.empty((top_k, order), dtype=np.int32)
+        sc = np.empty(top_k, dtype=np.float64)
+        rc = self._lib.oracle_scan_order_topk(_ptr(g), _ptr(p), g.shape[0], g.shape[1], order,
+                                              top_k, _ptr(x), _ptr(sc), threads)
+        if rc < 0:
+            raise ValueError("bad arguments or values")
+        return x, sc, rc
+
+
 _default = None
 
 
@@ -168,3 +212,15 @@ def pair_tables(genotypes, phenotype, pairs):
 
 def scan_pairs_topk(genotypes, phenotype, top_k, threads: int = 0):
     return default().scan_pairs_topk(genotypes, phenotype, top_k, threads)
+
+
+def tables_order(genotypes, phenotype, snps):
+    return default().tables_order(genotypes, phenotype, snps)
+
+
+def k2_cells(tables_):
+    return default().k2_cells(tables_)
+
+
+def scan_order_topk(genotypes, phenotype, order, top_k, threads: int = 0):
+    return default().scan_order_topk(genotypes, phenotype, order, top_k, threads)

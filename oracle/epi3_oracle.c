@@ -329,3 +329,195 @@ int oracle_scan_pairs_topk(const uint8_t* geno, const uint8_t* pheno, int32_t n_
     free(lf);
     return bad ? -1 : nt;
 }
+
+/* ---------------------------------------------------------------- any order
+ * Eq. 1 is stated for an interaction of any number of SNPs.  For `order` SNPs
+ * (x_0, ..., x_{order-1}) the table has 3^order cells per class; the cell of a
+ * sample is its genotypes read as base-3 digits, the first SNP most significant
+ * (cell = 9 gX + 3 gY + gZ for three SNPs, 3 gX + gY for two).  K2 is summed in
+ * cell order exactly as for the triplet.  order = 1 .. ORACLE_MAX_ORDER. */
+#define ORACLE_MAX_ORDER 6
+
+static int32_t cells_of(int32_t order) {
+    int32_t n = 1;
+    for (int32_t t = 0; t < order; ++t) n *= 3;
+    return n;
+}
+
+/* Frequency table of the SNPs snps[0..order); ft[c * 3^order + cell]. */
+static int count_order(const uint8_t* geno, const uint8_t* pheno, int64_t n_samples,
+                       int32_t order, const int32_t* snps, int32_t* ft) {
+    const int32_t ncell = cells_of(order);
+    memset(ft, 0, sizeof(int32_t) * 2 * (size_t)ncell);
+    for (int64_t s = 0; s < n_samples; ++s) {
+        int c = pheno[s];
+        if (c > 1) return -1;
+        int32_t cell = 0;
+        for (int32_t t = 0; t < order; ++t) {
+            int g = geno[(int64_t)snps[t] * n_samples + s];
+            if (g > 2) return -1;
+            cell = 3 * cell + g;
+        }
+        ft[c * ncell + cell] += 1;
+    }
+    return 0;
+}
+
+/* K2 of one 2 x ncell table, cell order 0..ncell-1, as k2_of_table. */
+static double k2_of_cells(const int32_t* ft, int32_t ncell, const double* lf) {
+    double k2 = 0.0;
+    for (int32_t cell = 0; cell < ncell; ++cell) {
+        int32_t r0 = ft[cell], r1 = ft[ncell + cell];
+        double term = (lf[r0 + r1 + 1] - lf[r0]) - lf[r1];
+        k2 = k2 + term;
+    }
+    return k2;
+}
+
+/* Tables of n SNP sets of the given order (distinct indices, in the given roles):
+ * snps [n][order], out [n][2][3^order].  Returns 0, or -1 on a bad order, index or value. */
+int oracle_tables_order(const uint8_t* geno, const uint8_t* pheno, int32_t n_snps,
+                        int64_t n_samples, int32_t order, int64_t n, const int32_t* snps,
+                        int32_t* out) {
+    if (order < 1 || order > ORACLE_MAX_ORDER) return -1;
+    const int32_t ncell = cells_of(order);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+    for (int64_t t = 0; t < n; ++t) {
+        const int32_t* x = snps + t * order;
+        for (int32_t q = 0; q < order; ++q)
+            if (x[q] < 0 || x[q] >= n_snps) bad = 1;
+        if (bad) continue;
+        if (count_order(geno, pheno, n_samples, order, x, out + t * 2 * ncell)) bad = 1;
+    }
+    return bad ? -1 : 0;
+}
+
+/* K2 of n tables [n][2][ncell]; out[n]. */
+int oracle_k2_cells(int64_t n, int32_t ncell, const int32_t* tables, double* out) {
+    int64_t rmax = 0;
+    for (int64_t t = 0; t < n; ++t)
+        for (int32_t cell = 0; cell < ncell; ++cell) {
+            int64_t r0 = tables[t * 2 * ncell + cell], r1 = tables[t * 2 * ncell + ncell + cell];
+            if (r0 < 0 || r1 < 0) return -1;
+            if (r0 + r1 > rmax) rmax = r0 + r1;
+        }
+    double* lf = (double*)malloc(sizeof(double) * (size_t)(rmax + 2));
+    if (!lf) return -2;
+    oracle_log_factorials((int32_t)(rmax + 1), lf);
+    for (int64_t t = 0; t < n; ++t) out[t] = k2_of_cells(tables + t * 2 * ncell, ncell, lf);
+    free(lf);
+    return 0;
+}
+
+typedef struct {
+    double k2;
+    int32_t x[ORACLE_MAX_ORDER];
+} entry_o;
+
+/* Total order: K2 ascending, then the SNP indices lexicographically. */
+static int before_o(const entry_o* a, const entry_o* b, int32_t order) {
+    if (a->k2 != b->k2) return a->k2 < b->k2;
+    for (int32_t t = 0; t < order; ++t)
+        if (a->x[t] != b->x[t]) return a->x[t] < b->x[t];
+    return 0;
+}
+
+static void keep_best_o(entry_o* list, int32_t* len, int32_t cap, const entry_o* e, int32_t order) {
+    int32_t n = *len;
+    if (n == cap && !before_o(e, &list[n - 1], order)) return;
+    int32_t pos = (n == cap) ? n - 1 : n;
+    while (pos > 0 && before_o(e, &list[pos - 1], order)) {
+        list[pos] = list[pos - 1];
+        --pos;
+    }
+    list[pos] = *e;
+    if (n < cap) *len = n + 1;
+}
+
+/* Exhaustive scan over every SNP set x_0 < x_1 < ... < x_{order-1}: the top_k sets by
+ * (K2, x_0, x_1, ...).  out_snps [top_k][order], out_k2 [top_k].  Returns the number of
+ * threads used (> 0) or a negative error. */
+int oracle_scan_order_topk(const uint8_t* geno, const uint8_t* pheno, int32_t n_snps,
+                           int64_t n_samples, int32_t order, int32_t top_k, int32_t* out_snps,
+                           double* out_k2, int32_t n_threads) {
+    if (order < 1 || order > ORACLE_MAX_ORDER || n_snps < order || top_k < 1) return -1;
+    double total_sets = 1.0;
+    for (int32_t t = 0; t < order; ++t) total_sets = total_sets * (double)(n_snps - t) / (double)(t + 1);
+    if ((double)top_k > total_sets + 0.5) return -1;
+    const int32_t ncell = cells_of(order);
+    double* lf = (double*)malloc(sizeof(double) * (size_t)(n_samples + 2));
+    if (!lf) return -2;
+    oracle_log_factorials((int32_t)(n_samples + 1), lf);
+    int nt = 1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+    nt = omp_get_max_threads();
+#endif
+    entry_o* lists = (entry_o*)malloc(sizeof(entry_o) * (size_t)top_k * nt);
+    int32_t* lens = (int32_t*)calloc((size_t)nt, sizeof(int32_t));
+    int bad = 0;
+#pragma omp parallel reduction(| : bad)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        entry_o* mine = lists + (size_t)tid * top_k;
+        int32_t* ft = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)ncell);
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t first = 0; first < n_snps; ++first) {
+            /* every increasing completion x_1 < ... < x_{order-1} of x_0 = first */
+            int32_t x[ORACLE_MAX_ORDER];
+            x[0] = first;
+            int32_t depth = 1;
+            if (order > 1) x[1] = first;
+            while (depth > 0) {
+                if (depth == order) {
+                    if (count_order(geno, pheno, n_samples, order, x, ft)) {
+                        bad = 1;
+                    } else {
+                        entry_o e;
+                        e.k2 = k2_of_cells(ft, ncell, lf);
+                        for (int32_t t = 0; t < order; ++t) e.x[t] = x[t];
+                        keep_best_o(mine, &lens[tid], top_k, &e, order);
+                    }
+                    --depth;
+                    continue;
+                }
+                /* next candidate at position depth (depth >= 1 here) */
+                ++x[depth];
+                if (x[depth] > n_snps - (order - depth)) {
+                    --depth;
+                    continue;
+                }
+                ++depth;
+                if (depth < order) x[depth] = x[depth - 1];
+            }
+        }
+        free(ft);
+    }
+    int32_t total = 0;
+    for (int t = 0; t < nt; ++t) {
+        memmove(lists + total, lists + (size_t)t * top_k, sizeof(entry_o) * lens[t]);
+        total += lens[t];
+    }
+    /* plain insertion sort of the merged lists (at most top_k * threads entries) */
+    for (int32_t a = 1; a < total; ++a) {
+        entry_o e = lists[a];
+        int32_t p = a;
+        while (p > 0 && before_o(&e, &lists[p - 1], order)) {
+            lists[p] = lists[p - 1];
+            --p;
+        }
+        lists[p] = e;
+    }
+    for (int32_t r = 0; r < top_k && r < total; ++r) {
+        for (int32_t t = 0; t < order; ++t) out_snps[r * order + t] = lists[r].x[t];
+        out_k2[r] = lists[r].k2;
+    }
+    free(lists);
+    free(lens);
+    free(lf);
+    return bad ? -1 : nt;
+}

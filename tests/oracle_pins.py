@@ -14,7 +14,11 @@ oracle's own code path as its expected value:
   SNP columns, and recovery of a strongly planted triplet (lowest K2 wins,
   Sec. III);
 * pairs (Eq. 1 for two SNPs, 9 cells): numpy bincount, big-integer K2, and the
-  triplet K2 of a monomorphic third SNP, which must equal the pair K2 exactly.
+  triplet K2 of a monomorphic third SNP, which must equal the pair K2 exactly;
+* any order (Eq. 1 for k SNPs, 3^k cells): numpy bincount of the base-3 cell,
+  big-integer K2, summing out a SNP gives the lower-order table, orders 2 and 3
+  equal the pair and triplet functions bit for bit, a monomorphic fourth SNP
+  gives the triplet K2 exactly, and numpy lexsort over every 4-SNP set.
 """
 from __future__ import annotations
 
@@ -289,8 +293,123 @@ def check_pair_ties_and_degenerate(o):
     assert math.isclose(sc[0], exact_pair_k2(numpy_pair_tables(g2, ph2, [[0, 1]])[0]), rel_tol=1e-13)
 
 
+# ---------------------------------------------------------------- any order (Eq. 1, k SNPs)
+def all_sets(m, order):
+    return np.array(list(itertools.combinations(range(m), order)), dtype=np.int32).reshape(-1, order)
+
+
+def numpy_order_tables(g, ph, sets):
+    """Independent counting: bincount of class*3^k + base-3 digits of the genotypes, the
+    first SNP most significant."""
+    order = sets.shape[1]
+    nc = 3 ** order
+    out = np.empty((len(sets), 2, nc), dtype=np.int64)
+    for t, x in enumerate(sets):
+        cell = np.zeros(g.shape[1], dtype=np.int64)
+        for snp in x:
+            cell = 3 * cell + g[snp].astype(np.int64)
+        out[t] = np.bincount(ph.astype(np.int64) * nc + cell, minlength=2 * nc).reshape(2, nc)
+    return out
+
+
+def exact_k2_cells(table):
+    """log of prod_cells (r+1)! / (r0! r1!) over any number of cells, with big integers."""
+    num = 1
+    for r0, r1 in zip(table[0], table[1]):
+        r0, r1 = int(r0), int(r1)
+        num *= math.factorial(r0 + r1 + 1) // (math.factorial(r0) * math.factorial(r1))
+    return math.log(num)
+
+
+def check_order_tables_bruteforce(o):
+    for (m, n, n1, seed, order) in [(7, 61, 25, 51, 4), (6, 130, 129, 52, 4), (6, 40, 17, 53, 5),
+                                    (5, 33, 10, 54, 1), (6, 97, 40, 55, 3)]:
+        g, ph = tiny_data(m, n, n1, seed)
+        sets = all_sets(m, order)
+        want = numpy_order_tables(g, ph, sets)
+        assert np.array_equal(o.tables_order(g, ph, sets), want)
+        rev = np.ascontiguousarray(sets[:, ::-1])           # roles matter: first SNP = top digit
+        assert np.array_equal(o.tables_order(g, ph, rev), numpy_order_tables(g, ph, rev))
+
+
+def check_order_k2_bigint(o):
+    g, ph = tiny_data(7, 90, 41, 56)
+    tabs = numpy_order_tables(g, ph, all_sets(7, 4))[:20]
+    got = o.k2_cells(tabs)
+    want = np.array([exact_k2_cells(t) for t in tabs])
+    assert np.allclose(got, want, rtol=1e-13)
+
+
+def check_order_marginals(o):
+    # summing an order-4 table over the last SNP's digit gives the table of the first three
+    # SNPs, and over the first SNP's digit the table of the last three
+    g, ph = tiny_data(8, 150, 66, 57)
+    sets = all_sets(8, 4)
+    t4 = o.tables_order(g, ph, sets).reshape(len(sets), 2, 3, 3, 3, 3)
+    assert np.array_equal(t4.sum(axis=5).reshape(len(sets), 2, 27),
+                          o.tables_order(g, ph, np.ascontiguousarray(sets[:, :3])))
+    assert np.array_equal(t4.sum(axis=2).reshape(len(sets), 2, 27),
+                          o.tables_order(g, ph, np.ascontiguousarray(sets[:, 1:])))
+    n1 = int(ph.sum())
+    assert np.all(t4.sum(axis=(2, 3, 4, 5)) == np.array([150 - n1, n1]))
+
+
+def check_order_matches_lower_orders(o):
+    # order 3 and order 2 of the generic functions are the triplet and pair functions exactly
+    g, ph = tiny_data(10, 120, 50, 58)
+    trip = all_triplets(10)
+    assert np.array_equal(o.tables_order(g, ph, trip), o.tables(g, ph, trip))
+    tr3, sc3, _ = o.scan_topk(g, ph, 25)
+    x3, s3, _ = o.scan_order_topk(g, ph, 3, 25)
+    assert np.array_equal(x3, tr3) and np.array_equal(s3, sc3)
+    pr, ps, _ = o.scan_pairs_topk(g, ph, 30)
+    x2, s2, _ = o.scan_order_topk(g, ph, 2, 30)
+    assert np.array_equal(x2, pr) and np.array_equal(s2, ps)
+
+
+def check_order_monomorphic(o):
+    # a monomorphic fourth SNP puts each triplet cell's counts at cell 3 c (the other 54 cells
+    # are empty and add exactly 0.0), so the 4-SNP K2 equals the triplet K2 bit for bit
+    g, ph = tiny_data(9, 170, 80, 59)
+    g[8] = 0
+    trip = all_triplets(8)
+    quads = np.concatenate([trip, np.full((len(trip), 1), 8, dtype=np.int32)], axis=1)
+    assert np.array_equal(o.k2_cells(o.tables_order(g, ph, quads)), o.scores(g, ph, trip))
+
+
+def check_order_scan_bruteforce(o):
+    for (m, n, n1, seed, k) in [(9, 70, 33, 60, 12), (8, 129, 64, 61, 70), (6, 31, 31, 62, 15),
+                                (7, 45, 20, 64, 35)]:                    # the last: every set
+        g, ph = tiny_data(m, n, n1, seed)
+        sets = all_sets(m, 4)
+        s = np.array([exact_k2_cells(t) for t in numpy_order_tables(g, ph, sets)])
+        s_oracle = o.k2_cells(o.tables_order(g, ph, sets))
+        assert np.allclose(s_oracle, s, rtol=1e-13)
+        rank = np.lexsort((sets[:, 3], sets[:, 2], sets[:, 1], sets[:, 0], s_oracle))
+        x, sc, _ = o.scan_order_topk(g, ph, 4, k)
+        assert np.array_equal(x, sets[rank[:k]])
+        assert np.array_equal(sc, s_oracle[rank[:k]])
+
+
+def check_order_ties(o):
+    # a duplicated SNP column gives 4-SNP sets with identical tables: equal K2, ordered by
+    # their indices
+    # (the copy sits in the same, last, role in both sets, so the cells line up one to one)
+    g, ph = tiny_data(9, 200, 95, 63)
+    g[8] = g[7]
+    x, sc, _ = o.scan_order_topk(g, ph, 4, 126)            # every 4-SNP set of 9
+    pos = {tuple(q): r for r, q in enumerate(x)}
+    for rest in itertools.combinations(range(7), 3):
+        a, b = rest + (7,), rest + (8,)
+        assert a in pos and b in pos
+        assert sc[pos[a]] == sc[pos[b]]
+        assert pos[a] < pos[b]
+
+
 ALL_CHECKS = [check_lf, check_hand_values, check_k2_bigint, check_tables_bruteforce,
               check_invariants, check_symmetries, check_monomorphic, check_degenerate,
               check_scan_bruteforce, check_ties, check_planted_recovery,
               check_pair_tables_bruteforce, check_pair_scan_bruteforce, check_pair_vs_triplet,
-              check_pair_ties_and_degenerate]
+              check_pair_ties_and_degenerate, check_order_tables_bruteforce, check_order_k2_bigint,
+              check_order_marginals, check_order_matches_lower_orders, check_order_monomorphic,
+              check_order_scan_bruteforce, check_order_ties]

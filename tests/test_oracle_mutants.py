@@ -22,6 +22,14 @@ MUTANTS = {
     "pair_classes_swapped": ("ft[c * NPCELL + 3 * a + b] += 1;",
                              "ft[(1 - c) * NPCELL + 3 * a + b] += 1;"),
     "pair_last_cell_skipped": ("cell < NPCELL; ++cell", "cell < NPCELL - 1; ++cell"),
+    "order_digits_reversed": ("cell = 3 * cell + g;", "cell = cell + g * cells_of(t);"),
+    "order_classes_swapped": ("ft[c * ncell + cell] += 1;", "ft[(1 - c) * ncell + cell] += 1;"),
+    "order_dropped_plus_one": ("double term = (lf[r0 + r1 + 1] - lf[r0]) - lf[r1];\n        k2 = k2 + term;\n    }\n    return k2;\n}\n\n/* Tables of n SNP sets",
+                               "double term = (lf[r0 + r1] - lf[r0]) - lf[r1];\n        k2 = k2 + term;\n    }\n    return k2;\n}\n\n/* Tables of n SNP sets"),
+    "order_last_snp_skips": ("if (x[depth] > n_snps - (order - depth)) {",
+                             "if (x[depth] > n_snps - (order - depth) - 1) {"),
+    "order_tiebreak_reversed": ("if (a->x[t] != b->x[t]) return a->x[t] < b->x[t];",
+                                "if (a->x[t] != b->x[t]) return a->x[t] > b->x[t];"),
     "pair_j_loop_skips": ("for (int32_t j = i + 1; j < n_snps; ++j) {\n                int32_t ft[2 * NPCELL];",
                           "for (int32_t j = i + 2; j < n_snps; ++j) {\n                int32_t ft[2 * NPCELL];"),
 }
