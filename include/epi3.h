@@ -38,7 +38,7 @@ extern "C" {
 #define EPI3_ERR_ARG (-1)         /* bad pointer, size, genotype > 2, phenotype > 1, top_k */
 #define EPI3_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
 #define EPI3_ERR_OOM (-3)         /* device or pinned host allocation failed */
-#define EPI3_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out (1 s) */
+#define EPI3_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out (about 1 s) */
 #define EPI3_ERR_UNSUPPORTED (-5) /* no sm_103 device, or a path/size this build lacks */
 #define EPI3_ERR_OVERFLOW (-6)    /* more near-tied candidates than the candidate stage holds */
 
@@ -126,6 +126,26 @@ int epi3_scan_range(epi3_handle* h, int64_t pair_begin, int64_t pair_end, int32_
  * EPI3_OK, EPI3_ERR_ARG (bad top_k or null pointers), EPI3_ERR_OOM or EPI3_ERR_CUDA.
  */
 int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* out_scores);
+
+/*
+ * Scan of any built interaction order (Eq. 1 is stated for any number of interacting SNPs):
+ * every set of `order` SNPs x_0 < ... < x_{order-1} gets its 3^order-cell x {control, case}
+ * table (cell = the genotypes read as base-3 digits, x_0 most significant: 9 gX + 3 gY + gZ
+ * for three) and its K2; the top_k sets by (K2 ascending, then the indices in order) are
+ * returned.
+ *   order        2 (= epi3_scan_pairs), 3 (= epi3_scan), or 4: every 4-SNP set counted by
+ *                AND + POPC over the bit planes (81 cells, plane 2 by NOR) and scored in FP64
+ *                in cell order 0..80 with the rescoring table (needs M >= 4, class sizes and
+ *                M below 65536, and at most 4 GiB of selection scratch, about
+ *                C(M,4) / 2048 * top_k * 32 bytes); other orders give EPI3_ERR_UNSUPPORTED.
+ *   top_k        1..min(EPI3_MAX_TOPK, C(M, order)).
+ *   out_snps     [top_k][order] int32, increasing within a row, 0-based.
+ *   out_scores   [top_k] FP64 K2, ascending.
+ * Outputs are host memory unless the handle was created with EPI3_DEVICE_PTRS.  Errors as
+ * epi3_scan_pairs.
+ */
+int epi3_scan_order(epi3_handle* h, int32_t order, int32_t top_k, int32_t* out_snps,
+                    double* out_scores);
 
 /* Release the handle's device memory, stream (if owned) and events. */
 int epi3_destroy(epi3_handle* h);

@@ -892,6 +892,57 @@ int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* o
     return EPI3_OK;
 }
 
+int epi3_scan_order(epi3_handle* h, int32_t order, int32_t top_k, int32_t* out_snps,
+                    double* out_scores) {
+    if (order == 2) return epi3_scan_pairs(h, top_k, out_snps, out_scores);
+    if (order == 3) return epi3_scan(h, top_k, out_snps, out_scores);
+    g_err.clear();
+    (void)cudaGetLastError();  // do not report an earlier call's error as ours
+    if (!h) return fail(EPI3_ERR_ARG, "null handle");
+    if (order != 4) return fail(EPI3_ERR_UNSUPPORTED, "interaction order %d (2, 3 and 4 are built)", order);
+    if (!out_snps || !out_scores) return fail(EPI3_ERR_ARG, "null output pointer");
+    if (h->M < 4) return fail(EPI3_ERR_ARG, "order 4 needs at least 4 SNPs");
+    const long long nq = quad_count(h->M);
+    if (top_k < 1 || top_k > EPI3_MAX_TOPK || top_k > nq)
+        return fail(EPI3_ERR_ARG, "top_k %d outside 1..min(%d, %lld)", top_k, EPI3_MAX_TOPK, nq);
+    if (h->N0 >= 65536 || h->N1 >= 65536 || h->M >= 65536)
+        return fail(EPI3_ERR_UNSUPPORTED, "the four-SNP scan needs class sizes and n_snps below 65536");
+    const size_t sel = (quad_scan_scratch(h->M, top_k) + 255) & ~(size_t)255;
+    if (sel > (size_t)4 << 30)
+        return fail(EPI3_ERR_UNSUPPORTED, "four-SNP scan of %d SNPs with top_k %d needs %zu bytes of "
+                    "selection scratch (limit 4 GiB)", h->M, top_k, sel);
+    const size_t need = sel + sizeof(double) * (size_t)top_k + sizeof(int32_t) * 4 * (size_t)top_k;
+    if (h->pair_scratch_bytes < need) {
+        cudaFree(h->d_pair_scratch);
+        h->d_pair_scratch = nullptr;
+        h->pair_scratch_bytes = 0;
+        CK(dev_alloc(&h->d_pair_scratch, need), "alloc four-SNP scan scratch");
+        h->pair_scratch_bytes = need;
+    }
+    double* d_s = reinterpret_cast<double*>(static_cast<char*>(h->d_pair_scratch) + sel);
+    int32_t* d_sets = reinterpret_cast<int32_t*>(d_s + top_k);
+    CK(cudaEventRecord(h->ev[0], h->stream), "event");
+    CK(launch_quad_scan(h->pl, h->k2.lf64, h->N0, h->N1, top_k, h->d_pair_scratch, d_sets, d_s,
+                        h->stream), "four-SNP scan launch");
+    CK(cudaEventRecord(h->ev[1], h->stream), "event");
+    const cudaMemcpyKind kind =
+        (h->flags & EPI3_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(out_snps, d_sets, sizeof(int32_t) * 4 * top_k, kind, h->stream),
+       "copy sets");
+    CK(cudaMemcpyAsync(out_scores, d_s, sizeof(double) * top_k, kind, h->stream), "copy scores");
+    CK(cudaStreamSynchronize(h->stream), "four-SNP scan");
+    epi3_stats& s = h->stats;
+    s.n_triplets = nq;  // sets scored
+    s.n_candidates = 0;
+    s.n_rescored = nq;
+    s.path = EPI3_PATH_POPC;
+    cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[0], h->ev[1]);
+    s.total_ms = s.scan_kernel_ms;
+    s.select_ms = 0.f;
+    (void)cudaGetLastError();
+    return EPI3_OK;
+}
+
 int epi3_tables(epi3_handle* h, int64_t n, const int32_t* triplets, int32_t* out_counts,
                 int32_t path) {
     g_err.clear();

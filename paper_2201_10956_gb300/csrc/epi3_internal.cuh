@@ -122,6 +122,12 @@ cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
 size_t pair_scan_scratch(long long n_pairs, int k);
 cudaError_t launch_pair_scan(const PairTables& pt, const double* lf64, int M, int k,
                              void* scratch, int32_t* out_pairs, double* out_s, cudaStream_t st);
+// Four-SNP scan (Eq. 1 for four SNPs, 81 cells): the k best sets by (FP64 K2, i, j, k, l) from
+// the bit planes; needs both class sizes below 65536 and M below 65536.
+long long quad_count(int M);
+size_t quad_scan_scratch(int M, int k);
+cudaError_t launch_quad_scan(const Planes& pl, const double* lf64, int n0, int n1, int k,
+                             void* scratch, int32_t* out_snps, double* out_s, cudaStream_t st);
 // max over n in [0, n_lf) of (n + 1/2) |lg2_hw(n + 1) - log2(n + 1)| (FP64) into *out (device).
 cudaError_t launch_approx_error(const double* lf64, int n_lf, double* out, cudaStream_t st);
 cudaError_t launch_pair_tables(const Planes& pl, int4* pt, int2* marg, long long n_pairs,

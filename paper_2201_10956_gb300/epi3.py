@@ -25,7 +25,8 @@ PATH_AUTO, PATH_POPC, PATH_POPC8, PATH_MMA, PATH_MMA16, PATH_MMA4 = 0, 1, 2, 3, 
 MAX_TOPK = 512
 
 # Every symbol the header declares; tests check the library exports all of them.
-SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_scan_pairs", "epi3_destroy",
+SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_scan_pairs", "epi3_scan_order",
+           "epi3_destroy",
            "epi3_last_error",
            "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
            "epi3_scan_noalloc", "epi3_scan_scores", "epi3_scan_checksum", "epi3_batch_create", "epi3_batch_scan",
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
         "epi3_scan": [P, I32, P, P],
         "epi3_scan_range": [P, I64, I64, I32, P, P, ctypes.POINTER(I32)],
         "epi3_scan_pairs": [P, I32, P, P],
+        "epi3_scan_order": [P, I32, I32, P, P],
         "epi3_destroy": [P],
         "epi3_last_error": [],
         "epi3_tables": [P, I64, P, P, I32],
@@ -210,6 +212,14 @@ class Handle:
         sc = self._alloc((top_k,), np.float64)
         _check(load().epi3_scan_pairs(self._h, int(top_k), _ptr(pairs), _ptr(sc)))
         return pairs, sc
+
+    def scan_order(self, order: int, top_k: int):
+        """Scan of interaction order 2, 3 or 4 (Eq. 1 for that many SNPs): top-k SNP sets
+        (int32 [k, order]) and FP64 K2 ([k])."""
+        sets = self._alloc((top_k, order), np.int32)
+        sc = self._alloc((top_k,), np.float64)
+        _check(load().epi3_scan_order(self._h, int(order), int(top_k), _ptr(sets), _ptr(sc)))
+        return sets, sc
 
     def tables(self, triplets, path: int = PATH_AUTO):
         t = self._triplets(triplets)
