@@ -141,14 +141,24 @@ def shard_pairs(m, world, rank):
     return pair_at(lo_t), pair_at(hi_t)
 
 
-PATH_NAMES = {1: "popc", 2: "popc8", 3: "mma", 4: "mma16", 5: "mma4"}
+PATH_NAMES = {1: "popc", 2: "popc8", 3: "mma", 4: "mma16", 5: "mma4", 6: "mma4c"}
 DTYPES = {1: "u32 popc / int32 counts", 2: "u32 popc / int32 counts",
           3: "e4m3 0/1 x e4m3 0/1 -> fp32 (exact integer counts)",
           4: "f16 0/1 x f16 0/1 -> fp32 (exact integer counts)",
-          5: "e2m1 0/1 x e2m1 0/1, ue8m0 block scales 1.0 -> fp32 (exact integer counts)"}
+          5: "e2m1 0/1 x e2m1 0/1, ue8m0 block scales 1.0 -> fp32 (exact integer counts)",
+          6: "e2m1 0/1 x e2m1 0/1 (sample-compacted), ue8m0 block scales 1.0 -> fp32 (exact integer counts)"}
 
 
-def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config):
+def compacted_fraction(genotypes):
+    """Share of sample-triplets (i < j < k, all samples) whose first SNP i has genotype 0 or 1,
+    i.e. the samples the compacted tensor form multiplies."""
+    m, n = genotypes.shape
+    not2 = (genotypes != 2).sum(axis=1).astype(np.float64)          # per SNP
+    later_pairs = np.array([(m - i - 1) * (m - i - 2) / 2 for i in range(m)])
+    return float((not2 * later_pairs).sum() / (gen.n_triplets(m) * n))
+
+
+def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config, cmp_frac=1.0):
     """Roofline of the dominant kernel, from algorithmic work per launch.
 
     POPC forms: 27 (paper's form) or 8 (8-cell form) 32-bit POPC per 32-sample word and
@@ -160,6 +170,19 @@ def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config):
     units = gen.n_triplets(m) * n / world          # sample-triplets per launch
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     traffic = TRAFFIC.get((PATH_NAMES.get(path), config))
+    if path == 6:
+        # sample-compacted form: 4 MACs per (triplet, sample with g_i in {0, 1}); cmp_frac is
+        # the share of sample-triplets whose first-SNP genotype is 0 or 1 (the others enter no
+        # set), computed from the data set
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 * 6.0
+        achieved = units * cmp_frac * 8.0 / kern_s / 1e12
+        return {"bound": "tensor", "kernel": "scan_cmp_kernel (e2m1)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst) x 6 (e2m1/bf16 nominal ratio)",
+                "work_note": f"8 FLOP (4 useful 0/1 MACs) per sample-triplet with a first-SNP "
+                             f"genotype in {{0,1}} ({cmp_frac:.4f} of all); tile waste excluded"}
     if path in (3, 4, 5):
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         ratio, elem = {3: (2.0, "e4m3"), 4: (1.0, "f16"), 5: (6.0, "e2m1")}[path]
@@ -447,7 +470,7 @@ def run_ours(args, rank, world, local_rank):
     peaks = read_peaks()
     kern_s = statistics.mean(kern_ms) / 1000.0
     roofline = roofline_of(st["path"], m, n, world, kern_s, props.multi_processor_count, peaks,
-                           args.config)
+                           args.config, cmp_frac=compacted_fraction(d.genotypes) if st["path"] == 6 else 1.0)
     roofline["kernel_ms"] = 1000 * kern_s
     roofline["select_ms"] = statistics.mean(sel_ms)
     # pack: genotype bytes in, phenotype in, two bit planes out (algorithmic bytes)

@@ -56,6 +56,11 @@ extern "C" {
 #define EPI3_PATH_MMA4 5  /* the same GEMM with FP4 E2M1 operands, two per byte, every 32-element
                              block scaled by 2^0 (tcgen05 kind::mxf4, FP32 accumulation); the
                              default (auto) scan path up to about 8700 SNPs, POPC8 beyond */
+#define EPI3_PATH_MMA4C 6 /* the 8 cells on sample-compacted FP4 E2M1 operands: per first SNP i,
+                             class and genotype a of i, the samples with g_i = a are gathered
+                             once, and n(a, b, z) = (one-hot rows (j, b)) x (one-hot rows (k, z))
+                             over those samples (tcgen05 kind::mxf4, both operands from shared
+                             memory, 4 MACs per sample-triplet); 19 cells derived */
 
 #define EPI3_MAX_TOPK 512
 
@@ -198,7 +203,7 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
 
 /*
  * Options (strings): "path" = "auto" (the default: EPI3_PATH_MMA4 up to about 8700 SNPs,
- * EPI3_PATH_POPC8 beyond) | "popc" | "popc8" | "mma" | "mma16" | "mma4";
+ * EPI3_PATH_POPC8 beyond) | "popc" | "popc8" | "mma" | "mma16" | "mma4" | "mma4c";
  * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
  * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);
  * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with
@@ -207,7 +212,9 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
  * tensor-core scan kernel's form: 14 warps with 128 registers each, or 16 warps that move
  * registers to the epilogue; "auto" takes the split form below a sample count where the
  * epilogue bounds the scan).  Unknown keys or values: EPI3_ERR_ARG, or EPI3_ERR_UNSUPPORTED
- * for a path that is not available.
+ * for a path that is not available.  "cmp_buffer_mb" = device memory (MiB, default 2048) for
+ * the compacted chunks of EPI3_PATH_MMA4C: the first SNPs are compacted and scanned in ranges
+ * whose chunks fit it (a range needs at least one first SNP's chunks).
  */
 int epi3_set_option(epi3_handle* h, const char* key, const char* value);
 
@@ -238,6 +245,9 @@ typedef struct {
        skipped without its exact FP32 score; the bound comes from the approximation's error
        measured on the device for every count 0..N+1 */
     float k2_prune_bound;
+    /* sample-compacted form (EPI3_PATH_MMA4C) with option "profile" = 1: device time of the
+       compaction kernels, a part of scan_kernel_ms (0 otherwise) */
+    float compact_ms;
 } epi3_stats;
 
 int epi3_get_stats(const epi3_handle* h, epi3_stats* out);

@@ -108,6 +108,11 @@ struct epi3_handle {
     bool profile = false;
     int mma_form = 0;                    // tensor scan: 0 = by sample count, 1 = plain, 2 = split
     unsigned long long* d_prof = nullptr;
+    uint8_t* d_cmp = nullptr;     // compacted chunks of the sample-compacted tensor form
+    size_t cmp_bytes = 0;
+    size_t cmp_cap = (size_t)2 << 30;  // option "cmp_buffer_mb": bytes of compacted chunks at once
+    CmpFirst* d_firsts = nullptr; // per first SNP: chunk bases, K-steps, tiles
+    std::vector<int2> h_marg;     // marginals on the host (the compacted sets' sizes)
     int4* d_tiles = nullptr;      // tile list of the tensor-core form
     long long n_tiles = 0, tiles_pb = -1, tiles_pe = -1;
     Ctrl* h_ctrl = nullptr;       // pinned
@@ -117,7 +122,8 @@ struct epi3_handle {
     int threads = 128;
     int ctas_per_sm = 0;
     bool timing = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // scan start, kernels start, kernels end, scan end; 4-5 bracket each compaction (profile)
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     epi3_stats stats{};
 };
 
@@ -140,6 +146,8 @@ void release(epi3_handle* h) {
     cudaFree(h->d_ptf);
     cudaFree(h->d_margf);
     cudaFree(h->d_oh);
+    cudaFree(h->d_cmp);
+    cudaFree(h->d_firsts);
     cudaFree(h->d_tiles);
     cudaFree(h->d_cd);
     cudaFree(h->d_prof);
@@ -318,8 +326,8 @@ int ensure_pair_tables(epi3_handle* h) {
 }
 
 // Tensor-core form: pre-tiled one-hot operand (built once per element type).
-int ensure_onehot(epi3_handle* h, int kind) {
-    if (!h->d_ptf) {  // the tensor scan's FP32 copies of the pair tables (built once)
+int ensure_pair_floats(epi3_handle* h) {
+    if (!h->d_ptf) {  // the tensor scans' FP32 copies of the pair tables (built once)
         const long long np = h->ptab.n_pairs;
         CK(dev_alloc((void**)&h->d_ptf, sizeof(float4) * 2 * (size_t)np), "alloc FP32 pair tables");
         CK(dev_alloc((void**)&h->d_margf, sizeof(float2) * 2 * (size_t)h->M), "alloc FP32 marginals");
@@ -328,6 +336,12 @@ int ensure_onehot(epi3_handle* h, int kind) {
         h->ptab.ptf = h->d_ptf;
         h->ptab.margf = h->d_margf;
     }
+    return EPI3_OK;
+}
+
+int ensure_onehot(epi3_handle* h, int kind) {
+    const int rc = ensure_pair_floats(h);
+    if (rc != EPI3_OK) return rc;
     if (h->d_oh && h->oh_kind == kind) return EPI3_OK;
     cudaFree(h->d_oh);
     h->d_oh = nullptr;
@@ -335,12 +349,15 @@ int ensure_onehot(epi3_handle* h, int kind) {
     // N_c samples plus the bias sample (position N_c) of a non-empty class
     const int ks0 = h->N0 ? h->N0 / spk + 1 : 0, ks1 = h->N1 ? h->N1 / spk + 1 : 0;
     const int kbc = (h->M + 63) / 64;
-    const size_t bytes = (size_t)kbc * (ks0 + ks1) * 16384;
-    CK(dev_alloc((void**)&h->d_oh, bytes), "alloc one-hot operand");
+    CK(dev_alloc((void**)&h->d_oh, onehot_bytes(h->M, ks0, ks1)), "alloc one-hot operand");
     h->oh_ks[0] = ks0;
     h->oh_ks[1] = ks1;
     h->oh_off1 = (long long)kbc * ks0;
     CK(launch_onehot(h->pl, h->d_oh, h->oh_off1, ks0, ks1, kbc, kind, h->stream), "one-hot launch");
+    uint8_t* yoh = h->d_oh + (size_t)kbc * (ks0 + ks1) * 16384;
+    uint8_t* xoh = yoh + (size_t)2 * kbc * (ks0 + ks1) * 8192;
+    CK(launch_onehot_views(h->d_oh, h->oh_off1, ks0, ks1, kbc, h->M, yoh, xoh, h->stream),
+       "one-hot views launch");
     CK(cudaStreamSynchronize(h->stream), "one-hot");
     h->oh_kind = kind;
     return EPI3_OK;
@@ -460,7 +477,10 @@ int finish_scan(epi3_handle* h, int top_k, int attempt) {
     CK(cudaStreamSynchronize(h->stream), "scan");
     const int st = h->h_ctrl->status;
     if (st & kStTimeout)
-        return fail(EPI3_ERR_TIMEOUT, "a bounded device-side wait of the scan ran out");
+        return fail(EPI3_ERR_TIMEOUT,
+                    "a bounded device-side wait of the scan ran out (role %u, tile %u, set %u, step %u, "
+                    "detail %#x, %u)", h->h_ctrl->wait_role, h->h_ctrl->wait_tile,
+                    h->h_ctrl->wait_set, h->h_ctrl->wait_step, h->h_ctrl->pad_[0], h->h_ctrl->pad_[1]);
     if (st & kStCandOverflow) {
         if (h->cand_cap >= (1LL << 24) || attempt >= 3)
             return fail(EPI3_ERR_OVERFLOW, "more than %lld FP32 candidates", h->cand_cap);
@@ -509,6 +529,13 @@ CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k)
     cd.pt = h->ptab;
     cd.oh = h->d_oh;
     cd.oh_off1 = h->oh_off1;
+    {
+        const size_t kbc = (size_t)(h->M + 63) / 64, nks = (size_t)h->oh_ks[0] + h->oh_ks[1];
+        cd.yoh = h->d_oh ? h->d_oh + kbc * nks * 16384 : nullptr;
+        cd.yoh_off1 = (long long)(2 * kbc) * h->oh_ks[0];
+        cd.xoh = h->d_oh ? cd.yoh + 2 * kbc * nks * 8192 : nullptr;
+        cd.xoh_off1 = (long long)h->M * h->oh_ks[0];
+    }
     cd.KS[0] = h->oh_ks[0];
     cd.KS[1] = h->oh_ks[1];
     cd.pair_begin = pb;
@@ -588,6 +615,160 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
     s.k2_prune_bound = h->k2.prune_delta;
+    s.compact_ms = 0.f;
+    cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
+    (void)cudaGetLastError();
+    return EPI3_OK;
+}
+
+// Sample-compacted tensor form: the first SNPs are taken in ranges whose compacted chunks fit
+// the handle's buffer; per range one compaction launch, then one scan launch over the range's
+// tiles (the candidate stage carries over from range to range).
+
+int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int top_k,
+                  int32_t* out_trip, double* out_scores, int32_t* n_out) {
+    const int M = h->M;
+    if (h->h_marg.empty()) {
+        h->h_marg.resize(2 * (size_t)M);
+        CK(cudaMemcpy(h->h_marg.data(), h->d_marg, sizeof(int2) * 2 * (size_t)M,
+                      cudaMemcpyDeviceToHost), "read marginals");
+    }
+    // first SNPs whose triplets can hold a pair of [pb, pe): every i below the last pair's j
+    int i_hi = M - 2;
+    if (pe > 0) {
+        const long long p = pe - 1;
+        long long jj = (long long)((1.0 + std::sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+        while (jj * (jj - 1) / 2 > p) --jj;
+        while ((jj + 1) * jj / 2 <= p) ++jj;
+        i_hi = (int)std::min<long long>(i_hi, jj);
+    }
+    std::vector<CmpFirst> firsts((size_t)std::max(i_hi, 0));
+    std::vector<int> range_start;   // first SNP of each range
+    std::vector<long long> range_chunks, range_tiles;
+    long long chunks = 0, tiles = 0;
+    size_t need = 0;
+    for (int i = 0; i < i_hi; ++i) {
+        CmpFirst& f = firsts[i];
+        f.b_lo = (i + 1) / 64;
+        for (int c = 0; c < 2; ++c)
+            for (int a = 0; a < 2; ++a) {
+                const int2 mg = h->h_marg[(size_t)c * M + i];
+                f.ks[2 * c + a] = (a == 0 ? mg.x : mg.y) / 256 + 1;  // + the bias sample
+            }
+        const long long ch = cmp_chunks_of(f, M);
+        if (range_start.empty() || (size_t)(chunks + ch) * 16384 > h->cmp_cap ||
+            i - range_start.back() >= 65535) {
+            if (!range_start.empty()) {
+                range_chunks.push_back(chunks);
+                range_tiles.push_back(tiles);
+            }
+            range_start.push_back(i);
+            chunks = 0;
+            tiles = 0;
+        }
+        long long bq = chunks;
+        const long long nblk = (M + 63) / 64 - f.b_lo;
+        for (int q = 0; q < kCmpSets; ++q) {
+            f.base[q] = bq;
+            bq += nblk * f.ks[q];
+        }
+        chunks = bq;
+        f.tiles = cmp_tiles_of(M, f.b_lo);
+        f.tile0 = tiles;
+        tiles += f.tiles;
+        need = std::max(need, (size_t)chunks * 16384);
+    }
+    if (!range_start.empty()) {
+        range_chunks.push_back(chunks);
+        range_tiles.push_back(tiles);
+    }
+    if (h->cmp_bytes < need) {
+        cudaFree(h->d_cmp);
+        h->d_cmp = nullptr;
+        h->cmp_bytes = 0;
+        CK(dev_alloc((void**)&h->d_cmp, need), "alloc compacted chunks");
+        h->cmp_bytes = need;
+    }
+    cudaFree(h->d_firsts);
+    h->d_firsts = nullptr;
+    if (!firsts.empty()) {
+        CK(dev_alloc((void**)&h->d_firsts, sizeof(CmpFirst) * firsts.size()), "alloc first-SNP table");
+        CK(cudaMemcpyAsync(h->d_firsts, firsts.data(), sizeof(CmpFirst) * firsts.size(),
+                           cudaMemcpyHostToDevice, h->stream), "upload first-SNP table");
+    }
+    const int grid = h->sm_count;
+    const int n_ranges = (int)range_start.size();
+    float compact_ms = 0.f;
+    for (int attempt = 0;; ++attempt) {
+        if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
+        CK(cudaEventRecord(h->ev[0], h->stream), "event");
+        CK(launch_reset(h->d_ctrl, h->stream), "reset launch");
+        if (h->tsum)  // a retried scan counts every table again: the checksum restarts with it
+            CK(cudaMemsetAsync(h->tsum, 0, 2 * kTsumSlots * sizeof(unsigned long long), h->stream),
+               "clear checksum slots");
+        if (h->profile) {
+            if (!h->d_prof) CK(dev_alloc((void**)&h->d_prof, 8 * sizeof(unsigned long long)), "alloc profile");
+            CK(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), h->stream), "clear profile");
+        }
+        compact_ms = 0.f;
+        CK(cudaEventRecord(h->ev[1], h->stream), "event");
+        for (int r = 0; r < n_ranges; ++r) {
+            const int i0 = range_start[r];
+            const int n = (r + 1 < n_ranges ? range_start[r + 1] : i_hi) - i0;
+            if (h->profile) CK(cudaEventRecord(h->ev[4], h->stream), "event");
+            CK(launch_compact(h->pl, h->d_firsts + i0, i0, n, h->d_cmp, h->stream), "compaction launch");
+            if (h->profile) {  // profiling only: the host waits for each compaction to time it
+                CK(cudaEventRecord(h->ev[5], h->stream), "event");
+                CK(cudaEventSynchronize(h->ev[5]), "compaction");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]);
+                compact_ms += ms;
+            }
+            CmpArgs a{};
+            a.cd = cohort_of(h, pb, pe, top_k);
+            a.firsts = h->d_firsts + i0;
+            a.i0 = i0;
+            a.n_first = n;
+            a.n_tiles = range_tiles[r];
+            a.cmp = h->d_cmp;
+            a.prof = h->profile ? h->d_prof : nullptr;
+            CK(launch_scan_cmp(a, grid, h->stream, h->tsum != nullptr || h->profile),
+               "compacted scan launch");
+        }
+        CK(cudaEventRecord(h->ev[2], h->stream), "event");
+        const int rc = finish_scan(h, top_k, attempt);
+        if (rc == 1) continue;
+        if (rc != EPI3_OK) return rc;
+        break;
+    }
+    const int rc = copy_out(h, out_trip, out_scores, n_out);
+    if (rc != EPI3_OK) return rc;
+    epi3_stats& s = h->stats;
+    s.n_triplets = nt;
+    s.n_candidates = h->h_ctrl->n_cand;
+    s.n_rescored = h->h_ctrl->n_final;
+    s.path = EPI3_PATH_MMA4C;
+    s.grid = grid;
+    s.block = 512;
+    s.kernel_launches = 2 * n_ranges + 3;
+    s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
+    s.wait_producers_tmem = s.mma_issue = 0.f;
+    s.compact_ms = compact_ms;
+    if (h->profile && h->d_prof) {
+        unsigned long long p[8];
+        CK(cudaMemcpy(p, h->d_prof, sizeof(p), cudaMemcpyDeviceToHost), "read profile");
+        const double tot = p[5] > 0 ? (double)p[5] : 1.0;
+        s.wait_loader = (float)(p[0] / tot);
+        s.wait_mma_operands = (float)(p[1] / tot);
+        s.wait_mma_accum = (float)(p[2] / tot);
+        s.wait_epilogue = (float)(p[4] / tot);
+        s.mma_issue = (float)(p[7] / tot);
+    }
+    s.k2_rel_bound = h->k2.rel;
+    s.k2_abs_bound = h->k2.abs_;
+    s.k2_prune_bound = h->k2.prune_delta;
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
@@ -613,7 +794,8 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     if (n_out) *n_out = 0;
     if (top_k == 0) return EPI3_OK;
     const int path = resolve_path(h);
-    if (path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8 && !is_mma_path(path))
+    if (path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8 && path != EPI3_PATH_MMA4C &&
+        !is_mma_path(path))
         return fail(EPI3_ERR_UNSUPPORTED, "path %d not available", path);
     const bool mma = is_mma_path(path);
     if (mma && mma_tile_estimate(h->M) > kMaxMmaTiles)
@@ -623,6 +805,12 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         if (rc == EPI3_OK && mma) rc = ensure_onehot(h, kind_of_path(path));
         if (rc == EPI3_OK && mma) rc = ensure_tiles(h, pb, pe);
         if (rc != EPI3_OK) return rc;
+    }
+    if (path == EPI3_PATH_MMA4C) {
+        int rc = ensure_pair_tables(h);
+        if (rc == EPI3_OK) rc = ensure_pair_floats(h);
+        if (rc != EPI3_OK) return rc;
+        return scan_cmp_impl(h, pb, pe, nt, top_k, out_trip, out_scores, n_out);
     }
     if (mma) return scan_mma_impl(h, path, pb, pe, nt, top_k, out_trip, out_scores, n_out);
 
@@ -716,6 +904,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
     s.k2_prune_bound = h->k2.prune_delta;
+    s.compact_ms = 0.f;
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&s.total_ms, h->ev[0], h->ev[3]);
@@ -1041,6 +1230,7 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
         else if (!strcmp(value, "mma")) h->path = EPI3_PATH_MMA;
         else if (!strcmp(value, "mma16")) h->path = EPI3_PATH_MMA16;
         else if (!strcmp(value, "mma4")) h->path = EPI3_PATH_MMA4;
+        else if (!strcmp(value, "mma4c")) h->path = EPI3_PATH_MMA4C;
         else return fail(EPI3_ERR_UNSUPPORTED, "path '%s' not available", value);
         return EPI3_OK;
     }
@@ -1058,6 +1248,14 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
     }
     if (!strcmp(key, "profile")) {
         h->profile = atoi(value) != 0;
+        return EPI3_OK;
+    }
+    if (!strcmp(key, "cmp_buffer_mb")) {
+        char* end = nullptr;
+        const long v = strtol(value, &end, 10);
+        if (!end || *end || v < 1 || v > (1L << 20))
+            return fail(EPI3_ERR_ARG, "cmp_buffer_mb must be 1..1048576");
+        h->cmp_cap = (size_t)v << 20;
         return EPI3_OK;
     }
     if (!strcmp(key, "mma_form")) {

@@ -36,7 +36,10 @@ struct Ctrl {
     float t_final;                // FP32 threshold of the rescoring stage
     float kth;                    // k-th smallest FP32 score
     unsigned int n_out;           // rows written to the result
-    unsigned int pad_[7];
+    // first bounded wait that ran out (0 = none): role + 1, then the tile, set and step it
+    // was on (diagnostics of EPI3_ERR_TIMEOUT)
+    unsigned int wait_role, wait_tile, wait_set, wait_step;
+    unsigned int pad_[3];
 };
 
 struct Cand {                     // one FP32 candidate
@@ -148,14 +151,22 @@ cudaError_t launch_tile_list(const int4* blocks, int n_blocks, int cohort, int4*
                              cudaStream_t st);
 cudaError_t launch_onehot(const Planes& pl, uint8_t* oh, long long off1, int KS0, int KS1,
                           int kb_count, int kind, cudaStream_t st);
+// bytes of the one-hot chunks and their two rearranged views (one allocation: oh | yoh | xoh)
+size_t onehot_bytes(int M, int KS0, int KS1);
+cudaError_t launch_onehot_views(const uint8_t* oh, long long off1, int KS0, int KS1, int kb_count,
+                                int M, uint8_t* yoh, uint8_t* xoh, cudaStream_t st);
 // One data set ("cohort") as the tensor-core scan sees it.  The kernel reads these from
 // device memory, one per tile (tile.w = cohort index), so one launch can scan many.
 struct CohortDev {
     Planes pl;
     K2Tables k2;
     PairTables pt;
-    const uint8_t* oh;        // pre-tiled one-hot A chunks
+    const uint8_t* oh;        // pre-tiled one-hot chunks [class][64-SNP block][K-step], 16 KB
     long long oh_off1;        // chunk index of class 1 (class 0 starts at 0)
+    const uint8_t* yoh;       // second-SNP rows [class][32-SNP block][K-step], 8 KB each
+    long long yoh_off1;       // 8 KB unit of class 1
+    const uint8_t* xoh;       // first-SNP rows [class][SNP][K-step], 256 B each
+    long long xoh_off1;       // 256 B unit of class 1
     int KS[2];                // K-steps per class
     long long pair_begin, pair_end;
     Ctrl* ctrl;
@@ -166,6 +177,38 @@ struct CohortDev {
     unsigned long long* tsum;     // optional: table checksum slots (table_sum), no pruning
     int inject_timeout;       // test hook: the MMA issuer first waits on a barrier nobody signals
 };
+
+// ---------------------------------------------------------------- sample-compacted tensor scan
+constexpr int kCmpSets = 4;      // (class, genotype 0/1 of the first SNP)
+// Per first SNP of a compaction range: the chunk index of (block b_lo, step 0) of each set and
+// the sets' K-steps; chunk (b, ks) of set q is base[q] + (b - b_lo) * ks[q] + ks.
+struct CmpFirst {
+    long long base[kCmpSets];
+    int ks[kCmpSets];
+    int b_lo;                    // first 64-SNP block holding an SNP after i
+    int tiles;                   // tiles of this first SNP
+    long long tile0;             // index of its first tile in the range
+};
+
+struct CmpArgs {
+    CohortDev cd;                // tables, candidate stage, pair range, test hooks
+    const CmpFirst* firsts;      // per first SNP of the range
+    int i0, n_first;
+    long long n_tiles;           // tiles of the range
+    const uint8_t* cmp;          // compacted chunks of the range
+    unsigned long long* prof;    // optional (instrumented kernel): wait cycles per role
+};
+// compacted chunks of one first SNP: 16 KB each
+inline long long cmp_chunks_of(const CmpFirst& f, int M) {
+    const long long nblk = (M + 63) / 64 - f.b_lo;
+    return nblk * ((long long)f.ks[0] + f.ks[1] + f.ks[2] + f.ks[3]);
+}
+int cmp_tiles_of(int M, int b_lo);            // tiles (64 j x 32 k) of one first SNP
+size_t scan_cmp_smem();
+// compaction of first SNPs i0 .. i0 + n_first - 1 into cmp (chunk indices from firsts)
+cudaError_t launch_compact(const Planes& pl, const CmpFirst* firsts, int i0, int n_first,
+                           uint8_t* cmp, cudaStream_t st);
+cudaError_t launch_scan_cmp(const CmpArgs& a, int grid, cudaStream_t st, bool checksum);
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
 // split: the register-split form of the kernel (mma_split_registers of the launch's samples

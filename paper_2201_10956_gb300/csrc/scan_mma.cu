@@ -45,10 +45,14 @@ namespace {
 
 constexpr int kKB = 64;                  // third SNPs per tile (B rows = 2 per SNP)
 constexpr int kJB = 32;                  // second SNPs per tile (A rows = 4 per SNP)
-// shared-memory ring (K, Y, X chunks of one step): sm_stages<kind>() = TMEM A stages + 2, since
-// a stage goes back to the loader only once its step's MMAs (kTm steps earlier) are complete
+// Shared-memory ring of kSmStages slots, one K-step each, every operand's slots contiguous.
+// Two consecutive K-steps of one (tile, class) segment that fall on an aligned slot pair (an
+// even slot and the next) arrive by ONE bulk copy per operand, signalled on the even slot's
+// barrier: every copy costs the SM's copy engine a fixed overhead of about 100 cycles besides
+// its bytes, so fewer, larger copies raise the operand intake.  A slot goes back to the loader
+// once the MMAs of its K-step are complete.
 constexpr int kSmStagesMax = 6;
-constexpr int kChunk = 16384;            // bytes of one operand stage: 128 rows x 128 B
+constexpr int kChunk = 16384;            // bytes of one operand step: 128 rows x 128 B
 // Warp roles, two layouts.  Plain form, 14 warps: 0 = operand loader + TMEM allocator, 1 = MMA
 // issuer, 2..9 = epilogue (two warps per TMEM lane quadrant), 10..13 = A producers (one thread
 // per TMEM lane); every warp has the 128 registers the 14 warps can have.  Register-split
@@ -85,13 +89,11 @@ constexpr int kTmStagesMax = 4;
 template <int kKind>
 __host__ __device__ constexpr int tm_stages() { return kKind == kKindE2M1 ? 3 : 4; }
 template <int kKind>
-__host__ __device__ constexpr int sm_stages() { return tm_stages<kKind>() + 2; }
-static_assert(4 + 2 <= kSmStagesMax, "shared-memory ring");
+__host__ __device__ constexpr int sm_stages() { return 6; }
+static_assert(kSmStagesMax % 2 == 0, "slot pairs");
 static_assert(kRegions * 128 + 4 * kProdCols <= kTmemCols, "tensor memory budget");
 static_assert(kRegions * 128 + 3 * kProdCols <= kSfCol, "tensor memory budget (E2M1)");
-constexpr int kCandCapMma = 1024;
 constexpr int kTRow = 80;                   // bytes per row of an epilogue transpose slab
-constexpr int kPruneAt = kCandCapMma / 2;   // local candidates that trigger a prune
 
 
 // D (+)= A * B^T with A (128 rows x 32 bytes of K) in tensor memory at column `a`; the E2M1
@@ -243,84 +245,6 @@ __device__ __forceinline__ void store_row(uint8_t* tile, uint32_t r, const uint3
     }
 }
 
-__device__ void sort_cands_epi(Cand* buf, int tid) {
-    for (int size = 2; size <= kCandCapMma; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < kCandCapMma / 2; t += kEpiThreads) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = ((lo & size) == 0);
-                const Cand x = buf[lo], y = buf[hi];
-                if ((x.s > y.s) == up) {
-                    buf[lo] = y;
-                    buf[hi] = x;
-                }
-            }
-            epi_bar();
-        }
-}
-
-struct EpiShared {
-    Cand buf[kCandCapMma];
-    int cnt, keep;
-    float tloc;
-};
-
-// Sort the buffer (cnt <= kCandCapMma entries), publish this CTA's band threshold, keep the
-// entries inside the band; spill to the global list when too many tie.  Called by all
-// epilogue threads.
-__device__ int epi_prune(const CohortDev& a, EpiShared& es, int cnt, int tid, bool final_flush) {
-    const float kInf = __int_as_float(0x7f800000);
-    if (cnt >= a.top_k) {
-        for (int idx = cnt + tid; idx < kCandCapMma; idx += kEpiThreads) es.buf[idx].s = kInf;
-        epi_bar();
-        sort_cands_epi(es.buf, tid);
-        if (tid == 0) {
-            const float tl = band_threshold(es.buf[a.top_k - 1].s, a.k2.rel, a.k2.abs_);
-            atomicMin(&a.ctrl->thr, __float_as_uint(tl));
-            es.tloc = fminf(es.tloc, tl);
-        }
-    }
-    if (tid == 0) es.keep = 0;
-    epi_bar();
-    const float t = fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr));
-    if (final_flush || cnt < a.top_k) {
-        for (int idx = tid; idx < cnt; idx += kEpiThreads) {
-            const Cand e = es.buf[idx];
-            if (e.s <= t) {
-                const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
-                if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
-                else atomicOr(&a.ctrl->status, kStCandOverflow);
-            }
-        }
-        epi_bar();
-        return 0;
-    }
-    int keep = 0;
-    for (int idx = tid; idx < cnt; idx += kEpiThreads) keep += (es.buf[idx].s <= t);
-    if (keep) atomicAdd(&es.keep, keep);
-    epi_bar();
-    int kept = es.keep;
-    if (kept > kPruneAt) {
-        for (int idx = tid; idx < kept; idx += kEpiThreads) {
-            const Cand e = es.buf[idx];
-            const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
-            if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
-            else atomicOr(&a.ctrl->status, kStCandOverflow);
-        }
-        kept = 0;
-    }
-    epi_bar();
-    return kept;
-}
-
-// A candidate straight to the cohort's global list (the local buffer is full).
-__device__ __forceinline__ void cand_global(const CohortDev& a, const Cand& e) {
-    const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
-    if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
-    else atomicOr(&a.ctrl->status, kStCandOverflow);
-}
-
 // Walks one CTA's sequence of (tile, class, K-step): tiles blockIdx.x + n * gridDim.x,
 // class 0 then class 1, K-steps of the tile's cohort (classes without samples skipped).
 struct StepCursor {
@@ -343,10 +267,11 @@ __device__ __forceinline__ void cursor_load(StepCursor& cu, const CohortDev* cds
     cu.ks = 0;
 }
 
+// Advance by n K-steps (the steps of one shared-memory stage, never past its segment).
 __device__ __forceinline__ void cursor_next(StepCursor& cu, const CohortDev* cds, const int4* tiles,
-                                            long long my_tiles) {
+                                            long long my_tiles, int n) {
     if (!cu.valid) return;
-    ++cu.ks;
+    cu.ks += n;
     if (cu.ks < (cu.c ? cu.ks1 : cu.ks0)) return;
     if (cu.c == 0 && cu.ks1 > 0) {
         cu.c = 1;
@@ -442,38 +367,41 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 StepCursor cu{};
                 cu.tl = 0;
                 cursor_load(cu, cds, tiles, my_tiles);
-                long long q = 0;
                 Ring rs{0, 0u};
-                for (; cu.valid; ++q, cursor_next(cu, cds, tiles, my_tiles)) {
+                uint32_t used = 0, fph = 0;  // slots whose full barrier was used / their parity
+                while (cu.valid) {
                     const int s = rs.s;
-                    if (!mbar_wait_t(emptyS0 + 8 * s, rs.ph ^ 1u, abort_flag, my_acc)) {
+                    const int nks = cu.c ? cu.ks1 : cu.ks0;
+                    // an even slot and the next take two steps of one segment in one copy
+                    const int n = ((s & 1) == 0 && cu.ks + 1 < nks) ? 2 : 1;
+                    if (!mbar_wait_t(emptyS0 + 8 * s, rs.ph ^ 1u, abort_flag, my_acc) ||
+                        (n == 2 && !mbar_wait_t(emptyS0 + 8 * (s + 1), rs.ph ^ 1u, abort_flag, my_acc))) {
                         fail(cu.cd);
                         break;
                     }
                     // K: one-hot rows (k, z) of the tile's 64 third SNPs; Y: rows (j, b) of its 32
-                    // second SNPs (half of their 64-SNP chunk); X: rows (i, 0), (i, 1).  All three
-                    // come from the same pre-tiled one-hot matrix of the class.
-                    const long long base_c = cu.c ? cu.cd->oh_off1 : 0;
-                    const int nks = cu.c ? cu.ks1 : cu.ks0;
-                    const uint8_t* oh = cu.cd->oh;
-                    const long long ca = base_c + (long long)cu.tile.z * nks + cu.ks;
-                    const long long cy = base_c + (long long)(cu.tile.y >> 1) * nks + cu.ks;
-                    const long long cx = base_c + (long long)(cu.tile.x >> 6) * nks + cu.ks;
-                    const uint32_t xr = 2u * (uint32_t)(cu.tile.x & 63);
+                    // second SNPs; X: rows (i, 0), (i, 1).  Each for the n consecutive K-steps,
+                    // contiguous in its array, so one bulk copy apiece.
+                    const long long ca = (cu.c ? cu.cd->oh_off1 : 0) + (long long)cu.tile.z * nks + cu.ks;
+                    const long long cy = (cu.c ? cu.cd->yoh_off1 : 0) + (long long)cu.tile.y * nks + cu.ks;
+                    const long long cx = (cu.c ? cu.cd->xoh_off1 : 0) + (long long)cu.tile.x * nks + cu.ks;
                     const uint32_t fb = fullS0 + 8 * s;
-                    mbar_arrive_tx(fb, kChunk + kYChunk + kXBytes);
-                    bulk_g2s(smem_u32(sK + s * kChunk), oh + ca * kChunk, kChunk, fb);
-                    bulk_g2s(smem_u32(sY + s * kYChunk), oh + cy * kChunk + (cu.tile.y & 1) * kYChunk,
-                             kYChunk, fb);
-                    bulk_g2s(smem_u32(sX + s * kXBytes), oh + cx * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128,
-                             kXBytes, fb);
+                    mbar_arrive_tx(fb, (unsigned)(n * (kChunk + kYChunk + kXBytes)));
+                    bulk_g2s(smem_u32(sK + s * kChunk), cu.cd->oh + ca * kChunk, (unsigned)(n * kChunk), fb);
+                    bulk_g2s(smem_u32(sY + s * kYChunk), cu.cd->yoh + cy * kYChunk, (unsigned)(n * kYChunk), fb);
+                    bulk_g2s(smem_u32(sX + s * kXBytes), cu.cd->xoh + cx * kXBytes, (unsigned)(n * kXBytes), fb);
+                    used |= 1u << s;
+                    fph ^= 1u << s;
                     ring_next(rs, kSmStages);
+                    if (n == 2) ring_next(rs, kSmStages);
+                    cursor_next(cu, cds, tiles, my_tiles, n);
                 }
-                // drain: the copies of the last stages issued must land before the CTA exits
-                for (long long d = (q > kSmStages ? q - kSmStages : 0); d < q; ++d) {
-                    const int s = (int)(d % kSmStages);
+                // drain: the copies issued must land before the CTA exits (each used barrier's
+                // last phase)
+                for (int b = 0; b < kSmStages; ++b) {
+                    if (!((used >> b) & 1u)) continue;
                     volatile int no_abort = 0;
-                    mbar_wait(fullS0 + 8 * s, (unsigned)((d / kSmStages) & 1), &no_abort);
+                    mbar_wait(fullS0 + 8 * b, ((fph >> b) & 1u) ^ 1u, &no_abort);
                 }
             }
         } else if (warp == kWarpMma) {
@@ -578,22 +506,31 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
         // loops with ring counters keep the per-step bookkeeping to a few integer operations.
         int t_prev = -1;  // TMEM stage of a store issued but not yet published
         Ring rS{0, 0u}, rT{0, 0u};
-        Ring rF{0, 0u};   // shared-memory stage of step q - kTm (released once its MMAs finish)
+        Ring rF{0, 0u};   // shared-memory slot of step q - kTm (released once its MMAs finish)
         int warm = 0;     // min(q, kTm)
+        uint32_t fph = 0; // parity of each slot's full barrier (toggled when a copy's last step is read)
         bool ok = true;
         for (long long tl = 0; tl < my_tiles && ok; ++tl) {
             const int4 tile = tiles[blockIdx.x + tl * gridDim.x];
             const CohortDev* cd = cds + tile.w;
-            const int nsteps = cd->KS[0] + cd->KS[1];
+            const int KS0 = cd->KS[0], KS1 = cd->KS[1];
+            const int nsteps = KS0 + KS1;
             const uint32_t xp = (2u * (uint32_t)(tile.x & 63) + (uint32_t)ga) & 7u;
             const uint8_t* xrow = sX + ga * 128;
             for (int q = 0; q < nsteps; ++q) {
                 const int s = rS.s, t = rT.s;
-                // the MMAs of step q - kTm have read TMEM stage t; the loader's copies of
-                // step q have landed
+                // the loader's pairing rule: an odd slot whose step follows one of the same segment
+                // arrived with it, on the even slot's barrier; a step on an even slot whose next
+                // step is in the same segment shares its copy with that step
+                const bool second = (s & 1) && q > 0 && q != KS0;
+                const bool first_of_two = !(s & 1) && q + 1 < nsteps && q + 1 != KS0;
+                const int fb = second ? s - 1 : s;
+                // the MMAs of step q - kTm have read TMEM stage t; the loader's copy of step q
+                // has landed
                 const bool got =
                     mbar_wait_t(emptyT0 + 8 * t, rT.ph ^ 1u, abort_flag, kProf ? &w_acc2 : nullptr) &&
-                    mbar_wait_t(fullS0 + 8 * s, rS.ph, abort_flag, my_acc);
+                    mbar_wait_t(fullS0 + 8 * fb, (fph >> fb) & 1u, abort_flag, my_acc);
+                if (!first_of_two) fph ^= 1u << fb;
                 // tcgen05.st is warp-collective: the whole warp goes on or stops together
                 if (!__all_sync(0xffffffffu, got)) {
                     fail(cd);
@@ -601,7 +538,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     break;
                 }
                 tc_fence_after();
-                if (warm == kTm) {  // step q - kTm is complete: its stage goes back to the loader
+                if (warm == kTm) {  // step q - kTm is complete: its slot goes back to the loader
                     if (warp == kProdWarp0 && lane == 0) mbar_arrive(emptyS0 + 8 * rF.s);
                     ring_next(rF, kSmStages);
                 } else {
@@ -661,7 +598,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
             const CohortDev& cd = cds[tile.w];
             if (tile.w != cur) {  // candidates are per cohort: flush the previous one's
                 epi_bar();  // the previous tile's count is settled
-                if (cur >= 0) epi_prune(cds[cur], es, min(es.cnt, kCandCapMma), tid, true);
+                if (cur >= 0) epi_prune<kEpiThreads>(cds[cur], es, min(es.cnt, kCandCap), tid, true);
                 if (tid == 0) {
                     es.cnt = 0;
                     es.tloc = __int_as_float(0x7f800000);
@@ -814,7 +751,7 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                     }
                     if (s <= fminf(es.tloc, thr_g)) {
                         const int idx = atomicAdd(&es.cnt, 1);
-                        if (idx < kCandCapMma) es.buf[idx] = Cand{s, i, j, k};
+                        if (idx < kCandCap) es.buf[idx] = Cand{s, i, j, k};
                         else cand_global(cd, Cand{s, i, j, k});
                     }
                 }
@@ -827,15 +764,15 @@ scan_mma_kernel(const CohortDev* __restrict__ cds, const int4* __restrict__ tile
                 mbar_arrive(regE0 + 8 * reg1);
             }
             epi_bar();  // every append of this tile is in
-            const int cnt = min(es.cnt, kCandCapMma);
+            const int cnt = min(es.cnt, kCandCap);
             if (cnt > kPruneAt) {  // uniform: every thread read the same count
                 epi_bar();
-                const int kept = epi_prune(cd, es, cnt, tid, false);
+                const int kept = epi_prune<kEpiThreads>(cd, es, cnt, tid, false);
                 if (tid == 0) es.cnt = kept;
             }
         }
         epi_bar();
-        if (cur >= 0) epi_prune(cds[cur], es, min(es.cnt, kCandCapMma), tid, true);
+        if (cur >= 0) epi_prune<kEpiThreads>(cds[cur], es, min(es.cnt, kCandCap), tid, true);
         if (kProf && cur >= 0 && cds[cur].tsum) table_sum_flush(cds[cur].tsum, sum_h, sum_n);
     }
     if (kProf && prof) {
@@ -890,6 +827,46 @@ __global__ void onehot_kernel(Planes pl, uint8_t* __restrict__ oh, long long off
     }
 }
 
+// Two rearranged copies of the one-hot chunks, so that every operand of a shared-memory stage
+// (kStageKs consecutive K-steps) is one contiguous bulk copy:
+//   yoh: the rows (j, b) of 32 second SNPs, [class][32-SNP block][K-step], 8 KB each (the half
+//        of the 64-SNP chunk that holds them);
+//   xoh: the two rows (i, 0), (i, 1) of one first SNP, [class][SNP][K-step], 256 B each (as
+//        they sit in the swizzled chunk: an aligned pair of rows of one 8-row group).
+__global__ void onehot_views_kernel(const uint8_t* __restrict__ oh, long long off1, int KS0, int KS1,
+                                    int kb_count, int M, uint8_t* __restrict__ yoh,
+                                    uint8_t* __restrict__ xoh) {
+    const long long nks = KS0 + KS1;
+    const long long ny = (long long)2 * kb_count * nks * (kYChunk / 16);   // uint4 units of yoh
+    const long long nx = (long long)M * nks * (kXBytes / 16);             // uint4 units of xoh
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ny + nx;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < ny) {
+            const long long piece = t / (kYChunk / 16), u = t % (kYChunk / 16);
+            // piece in [class][jb32][ks] order
+            const int c = piece < 2LL * kb_count * KS0 ? 0 : 1;
+            const long long p = c ? piece - 2LL * kb_count * KS0 : piece;
+            const int KS = c ? KS1 : KS0;
+            const long long jb32 = p / KS, ks = p % KS;
+            const long long chunk = (c ? off1 + (jb32 >> 1) * KS1 : (jb32 >> 1) * KS0) + ks;
+            reinterpret_cast<uint4*>(yoh)[t] = reinterpret_cast<const uint4*>(
+                oh + chunk * kChunk + (jb32 & 1) * kYChunk)[u];
+        } else {
+            const long long tx = t - ny;
+            const long long piece = tx / (kXBytes / 16), u = tx % (kXBytes / 16);
+            // piece in [class][i][ks] order
+            const int c = piece < (long long)M * KS0 ? 0 : 1;
+            const long long p = c ? piece - (long long)M * KS0 : piece;
+            const int KS = c ? KS1 : KS0;
+            const long long i = p / KS, ks = p % KS;
+            const long long chunk = (c ? off1 + (i >> 6) * KS1 : (i >> 6) * KS0) + ks;
+            const uint32_t xr = 2u * (uint32_t)(i & 63);
+            reinterpret_cast<uint4*>(xoh)[tx] = reinterpret_cast<const uint4*>(
+                oh + chunk * kChunk + (xr >> 3) * 1024 + (xr & 7) * 128)[u];
+        }
+    }
+}
+
 // Tile list of a whole scan on the device: block b = {kb, jb, count, offset} of (third-SNP
 // block, second-SNP block) gets tiles (i, jb, kb, cohort) for i = 0 .. count-1 at offset + i.
 __global__ void tile_list_kernel(const int4* __restrict__ blocks, int cohort, int4* __restrict__ tiles) {
@@ -913,6 +890,22 @@ cudaError_t launch_tile_list(const int4* blocks, int n_blocks, int cohort, int4*
                              cudaStream_t st) {
     if (n_blocks == 0) return cudaSuccess;
     tile_list_kernel<<<n_blocks, 256, 0, st>>>(blocks, cohort, tiles);
+    return cudaGetLastError();
+}
+
+size_t onehot_bytes(int M, int KS0, int KS1) {
+    const size_t kbc = (size_t)(M + 63) / 64, nks = (size_t)KS0 + KS1;
+    return kbc * nks * kChunk + 2 * kbc * nks * kYChunk + (size_t)M * nks * kXBytes;
+}
+
+cudaError_t launch_onehot_views(const uint8_t* oh, long long off1, int KS0, int KS1, int kb_count,
+                                int M, uint8_t* yoh, uint8_t* xoh, cudaStream_t st) {
+    const long long units = ((long long)2 * kb_count * (KS0 + KS1) * (kYChunk / 16)) +
+                            ((long long)M * (KS0 + KS1) * (kXBytes / 16));
+    if (units == 0) return cudaSuccess;
+    const long long want = (units + 255) / 256;
+    const int blocks = (int)(want < 65535LL * 8 ? want : 65535LL * 8);
+    onehot_views_kernel<<<blocks, 256, 0, st>>>(oh, off1, KS0, KS1, kb_count, M, yoh, xoh);
     return cudaGetLastError();
 }
 

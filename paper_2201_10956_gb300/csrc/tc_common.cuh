@@ -73,6 +73,36 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(mbar) : "memory");
 }
+// Warp-wide forms: the whole (converged) warp executes the instruction and elect.sync lets one
+// lane issue it.  tcgen05.mma / commit and bulk copies take their operands in uniform registers:
+// issued by one lane inside a divergent branch, each costs an operand conversion that measured
+// about 69 cycles per MMA on GB300 (48 cycles for an M=128 N=64 MMA issued warp-wide, which is
+// its shared-memory operand read at 128 B/clk).  elect.sync picks the same leader every time in a
+// full warp, so a commit covers the MMAs that the same lane issued.
+__device__ __forceinline__ void mbar_arrive_tx_elect(uint32_t a, unsigned bytes) {
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n}\n"
+        ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_elect(uint32_t dst, const void* src, unsigned bytes,
+                                               uint32_t mbar) {
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n}\n"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_commit_elect(uint32_t mbar) {
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
+        ::"r"(mbar) : "memory");
+}
+// A value every lane holds alike, made provably warp-uniform for the compiler.
+__device__ __forceinline__ int warp_uniform(int v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ long long warp_uniform(long long v) {
+    return __shfl_sync(0xffffffffu, v, 0);
+}
 __device__ __forceinline__ void tc_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -244,6 +274,107 @@ __device__ __forceinline__ bool counts_of(const float* u0, const float* u1, int 
     return ok;
 }
 
+
+
+// ------------------------------------------------------------------ candidate stage
+// Named barrier 1 over the epilogue threads (kThreads of them); the variant also returns
+// whether any of them passed true.
+template <int kThreads>
+__device__ __forceinline__ void epi_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+template <int kThreads>
+__device__ __forceinline__ bool epi_sync_or(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 1, %2, a;\n"
+        " selp.u32 %0, 1, 0, b;\n}\n"
+        : "=r"(r) : "r"((uint32_t)p), "n"(kThreads) : "memory");
+    return r != 0;
+}
+
+constexpr int kCandCap = 1024;               // per-CTA candidate buffer (power of two)
+constexpr int kPruneAt = kCandCap / 2;       // local candidates that trigger a prune
+
+template <int kThreads>
+__device__ void sort_cands(Cand* buf, int tid) {
+    for (int size = 2; size <= kCandCap; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < kCandCap / 2; t += kThreads) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const Cand x = buf[lo], y = buf[hi];
+                if ((x.s > y.s) == up) {
+                    buf[lo] = y;
+                    buf[hi] = x;
+                }
+            }
+            epi_sync<kThreads>();
+        }
+}
+
+struct EpiShared {
+    Cand buf[kCandCap];
+    int cnt, keep;
+    float tloc;
+};
+
+// Sort the buffer (cnt <= kCandCap entries), publish this CTA's band threshold, keep the
+// entries inside the band; spill to the global list when too many tie.  Called by all
+// epilogue threads.
+template <int kThreads>
+__device__ int epi_prune(const CohortDev& a, EpiShared& es, int cnt, int tid, bool final_flush) {
+    const float kInf = __int_as_float(0x7f800000);
+    if (cnt >= a.top_k) {
+        for (int idx = cnt + tid; idx < kCandCap; idx += kThreads) es.buf[idx].s = kInf;
+        epi_sync<kThreads>();
+        sort_cands<kThreads>(es.buf, tid);
+        if (tid == 0) {
+            const float tl = band_threshold(es.buf[a.top_k - 1].s, a.k2.rel, a.k2.abs_);
+            atomicMin(&a.ctrl->thr, __float_as_uint(tl));
+            es.tloc = fminf(es.tloc, tl);
+        }
+    }
+    if (tid == 0) es.keep = 0;
+    epi_sync<kThreads>();
+    const float t = fminf(es.tloc, __uint_as_float(*(volatile unsigned*)&a.ctrl->thr));
+    if (final_flush || cnt < a.top_k) {
+        for (int idx = tid; idx < cnt; idx += kThreads) {
+            const Cand e = es.buf[idx];
+            if (e.s <= t) {
+                const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
+                if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
+                else atomicOr(&a.ctrl->status, kStCandOverflow);
+            }
+        }
+        epi_sync<kThreads>();
+        return 0;
+    }
+    int keep = 0;
+    for (int idx = tid; idx < cnt; idx += kThreads) keep += (es.buf[idx].s <= t);
+    if (keep) atomicAdd(&es.keep, keep);
+    epi_sync<kThreads>();
+    int kept = es.keep;
+    if (kept > kPruneAt) {
+        for (int idx = tid; idx < kept; idx += kThreads) {
+            const Cand e = es.buf[idx];
+            const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
+            if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
+            else atomicOr(&a.ctrl->status, kStCandOverflow);
+        }
+        kept = 0;
+    }
+    epi_sync<kThreads>();
+    return kept;
+}
+
+// A candidate straight to the cohort's global list (the local buffer is full).
+__device__ __forceinline__ void cand_global(const CohortDev& a, const Cand& e) {
+    const unsigned pos = atomicAdd(&a.ctrl->n_cand, 1u);
+    if (pos < (unsigned long long)a.cand_cap) a.cand[pos] = e;
+    else atomicOr(&a.ctrl->status, kStCandOverflow);
+}
 
 }  // namespace
 }  // namespace epi3

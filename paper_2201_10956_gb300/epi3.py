@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libepi3.so")
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OVERFLOW = -1, -2, -3, -4, -5, -6
 DEVICE_PTRS = 1
-PATH_AUTO, PATH_POPC, PATH_POPC8, PATH_MMA, PATH_MMA16, PATH_MMA4 = 0, 1, 2, 3, 4, 5
+PATH_AUTO, PATH_POPC, PATH_POPC8, PATH_MMA, PATH_MMA16, PATH_MMA4, PATH_MMA4C = 0, 1, 2, 3, 4, 5, 6
 MAX_TOPK = 512
 
 # Every symbol the header declares; tests check the library exports all of them.
@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("wait_loader", ctypes.c_float), ("wait_mma_operands", ctypes.c_float),
                 ("wait_mma_accum", ctypes.c_float), ("wait_producers", ctypes.c_float),
                 ("wait_epilogue", ctypes.c_float), ("wait_producers_tmem", ctypes.c_float),
-                ("mma_issue", ctypes.c_float), ("k2_prune_bound", ctypes.c_float)]
+                ("mma_issue", ctypes.c_float), ("k2_prune_bound", ctypes.c_float),
+                ("compact_ms", ctypes.c_float)]
 
 
 _lib = None

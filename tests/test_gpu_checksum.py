@@ -17,7 +17,7 @@ import paper_2201_10956_gb300 as epi
 pytestmark = pytest.mark.gpu
 
 PATHS = {"popc": epi.PATH_POPC, "popc8": epi.PATH_POPC8, "mma": epi.PATH_MMA,
-         "mma16": epi.PATH_MMA16, "mma4": epi.PATH_MMA4}
+         "mma16": epi.PATH_MMA16, "mma4": epi.PATH_MMA4, "mma4c": epi.PATH_MMA4C}
 M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
@@ -126,6 +126,7 @@ def test_medium_workload_all_tables_equal_oracle():
     assert want[1] == 1024 * 1023 * 1022 // 6
     with epi.Handle(d.genotypes, d.phenotype) as h:
         assert h.scan_checksum(epi.PATH_POPC8) == want
+        assert h.scan_checksum(epi.PATH_MMA4C) == want
         for form in ("plain", "split"):
             h.set_option("mma_form", form)
             assert h.scan_checksum(epi.PATH_MMA4) == want, form
@@ -140,13 +141,13 @@ def test_full_size_tables_agree(config):
     with epi.Handle(d.genotypes, d.phenotype) as h:
         ref = h.scan_checksum(epi.PATH_POPC8)
         assert ref[1] == m * (m - 1) * (m - 2) // 6
-        for name in ("mma4", "mma"):
+        for name in ("mma4", "mma", "mma4c"):
             assert h.scan_checksum(PATHS[name]) == ref, name
         h.set_option("mma_form", "split" if config == "large" else "plain")  # the other form
         assert h.scan_checksum(epi.PATH_MMA4) == ref
 
 
-@pytest.mark.parametrize("name", ["popc8", "mma4"])
+@pytest.mark.parametrize("name", ["popc8", "mma4", "mma4c"])
 def test_retried_scan_restarts_the_checksum(monkeypatch, name):
     # a 128-entry candidate list overflows, so the scan is retried with a larger one; the
     # retry counts every table again and the checksum must count it once

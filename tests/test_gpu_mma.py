@@ -18,8 +18,9 @@ import paper_2201_10956_gb300 as epi
 pytestmark = pytest.mark.gpu
 
 KERNEL_PATHS = [("popc", epi.PATH_POPC), ("popc8", epi.PATH_POPC8), ("mma", epi.PATH_MMA),
-                ("mma16", epi.PATH_MMA16), ("mma4", epi.PATH_MMA4)]
-TENSOR = {"mma": epi.PATH_MMA, "mma16": epi.PATH_MMA16, "mma4": epi.PATH_MMA4}
+                ("mma16", epi.PATH_MMA16), ("mma4", epi.PATH_MMA4), ("mma4c", epi.PATH_MMA4C)]
+TENSOR = {"mma": epi.PATH_MMA, "mma16": epi.PATH_MMA16, "mma4": epi.PATH_MMA4,
+          "mma4c": epi.PATH_MMA4C}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -117,8 +118,8 @@ def test_tensor_scan_medium_sampled(name):
     assert np.array_equal(oracle.scores(g, ph, tr), sc)
 
 
-@pytest.mark.parametrize("name", ["mma", "mma4"])
-@pytest.mark.parametrize("form", ["plain", "split"])
+@pytest.mark.parametrize("name,form", [("mma", "plain"), ("mma", "split"), ("mma4", "plain"),
+                                       ("mma4", "split"), ("mma4c", "auto")])
 def test_bounded_wait_times_out_and_context_survives(monkeypatch, name, form):
     # a device wait that can only run out: the kernel must report EPI3_ERR_TIMEOUT after its
     # 1 s limit, release its resources, and leave the context usable (both kernel forms)
@@ -181,7 +182,7 @@ def test_tensor_scan_full_size_matches_popc8(name):
     assert tuple(tr[0]) in [tuple(p) for p in d.planted]
 
 
-@pytest.mark.parametrize("name", ["mma4", "popc8"])
+@pytest.mark.parametrize("name", ["mma4", "mma4c", "popc8"])
 def test_largest_sample_count(name):
     # 131 072 samples, the most a handle takes: the widest log-factorial table, the loosest
     # pruning bound and 512 K-steps per class boundary; top-k still equals the oracle's
@@ -189,7 +190,7 @@ def test_largest_sample_count(name):
     with epi.Handle(g, ph) as h:
         h.set_option("path", name)
         tr, sc = h.scan(20)
-        if name == "mma4":
+        if name.startswith("mma4"):
             assert 0.0 < h.stats()["k2_prune_bound"] < 256.0
     otr, osc, _ = oracle.scan_topk(g, ph, 20)
     assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
