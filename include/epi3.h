@@ -202,16 +202,20 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores);
 int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t* out_count);
 
 /*
- * Options (strings): "path" = "auto" (the default: EPI3_PATH_MMA4 up to about 8700 SNPs,
- * EPI3_PATH_POPC8 beyond) | "popc" | "popc8" | "mma" | "mma16" | "mma4" | "mma4c";
+ * Options (strings): "path" = "auto" (the default: the form a tuner measures fastest for the
+ * shape, among EPI3_PATH_POPC8, EPI3_PATH_MMA4C and both forms of EPI3_PATH_MMA4 (which serves
+ * up to about 8700 SNPs); the first auto scan of a (n_snps / 64, n_samples / 1024) bucket
+ * times each on the heaviest slice of pairs, at most 1/16 of them, and the choice is kept for
+ * the process and appended to the file named by the environment variable EPI3_TUNE_CACHE,
+ * if set, for later processes) | "popc" | "popc8" | "mma" | "mma16" | "mma4" | "mma4c";
+ * "autotune" = "1" (default) | "0" (no measuring: auto = EPI3_PATH_MMA4C, form plain);
  * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
  * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);
  * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with
  * epi3_get_stats); "profile" = "0" | "1" (per-role wait accounting inside the tensor-core
  * scan kernel, reported in epi3_stats); "mma_form" = "auto" | "plain" | "split" (the
  * tensor-core scan kernel's form: 14 warps with 128 registers each, or 16 warps that move
- * registers to the epilogue; "auto" takes the split form below a sample count where the
- * epilogue bounds the scan).  Unknown keys or values: EPI3_ERR_ARG, or EPI3_ERR_UNSUPPORTED
+ * registers to the epilogue; "auto" lets the tuner time both for the shape).  Unknown keys or values: EPI3_ERR_ARG, or EPI3_ERR_UNSUPPORTED
  * for a path that is not available.  "cmp_buffer_mb" = device memory (MiB, default 2048) for
  * the compacted chunks of EPI3_PATH_MMA4C: the first SNPs are compacted and scanned in ranges
  * whose chunks fit it (a range needs at least one first SNP's chunks).
@@ -320,6 +324,13 @@ int epi3_batch_destroy(epi3_batch* b);
 int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out);
 /* The path (EPI3_PATH_MMA4 or EPI3_PATH_POPC8) the tuner chose for each cohort. */
 int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths);
+/* The tensor-scan form of each cohort: 0 = not a tensor cohort, 1 = plain, 2 = register-split,
+ * -1 = not measured yet.  All tensor cohorts share one persistent launch and so one form,
+ * measured on the first epi3_batch_scan by replaying the batch in both forms (the environment
+ * variable EPI3_BATCH_FORM = "plain" | "split" forces one).  The tile (128 rows (j, b) x 256
+ * columns (k, z) of the one-hot operands) is the kernel's only one: the tensor-memory budget
+ * of the split form's accumulator ring admits no other. */
+int epi3_batch_get_forms(const epi3_batch* b, int32_t* out_forms);
 /* One-shot: epi3_batch_create + epi3_batch_scan + epi3_batch_destroy. */
 int epi3_scan_batch(int32_t n_cohorts, const epi3_cohort* cohorts, int32_t top_k,
                     int32_t* out_triplets, double* out_scores, int32_t flags, void* cuda_stream);

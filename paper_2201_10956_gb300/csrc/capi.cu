@@ -106,7 +106,15 @@ struct epi3_handle {
     unsigned long long* tsum = nullptr;  // checksum slots of epi3_scan_checksum (that call only)
     CohortDev* d_cd = nullptr;    // this data set's descriptor for the tensor-core kernel
     bool profile = false;
-    int mma_form = 0;                    // tensor scan: 0 = by sample count, 1 = plain, 2 = split
+    int mma_form = 0;                    // tensor scan: 0 = measured (tuner), 1 = plain, 2 = split
+    int tuned_path = 0;                  // path "auto": the tuner's choice (0 = not yet measured)
+    int tuned_form = 0;                  // the tuner's tensor-scan form (1 plain, 2 split)
+    int tuned_form_path = 0;             // ... for this tensor path
+    bool autotune = true;                // option "autotune"
+    bool tuning = false;                 // a tuning scan is running
+    // last compacted-form scan: its plan's work terms and (tuning scans) compaction time
+    double last_cmp_chunks = 0.0, last_cmp_steps = 0.0;
+    float last_compact_ms = 0.f;
     unsigned long long* d_prof = nullptr;
     uint8_t* d_cmp = nullptr;     // compacted chunks of the sample-compacted tensor form
     size_t cmp_bytes = 0;
@@ -449,12 +457,13 @@ int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
 long long mma_tile_estimate(long long M) { return M * M * M / 12288 + 1; }
 constexpr long long kMaxMmaTiles = 1LL << 26;
 
-// auto: the tensor-core form (block-scaled E2M1 operands, the fastest measured) when its
-// tile list is small enough, else the 8-cell POPC form.
+// auto: the path the tuner measured fastest for this shape (tune_handle); with option
+// "autotune" = 0, the sample-compacted tensor form, which serves every shape.
 int resolve_path(const epi3_handle* h) {
     if (h->path != EPI3_PATH_AUTO) return h->path;
-    return mma_tile_estimate(h->M) <= kMaxMmaTiles ? EPI3_PATH_MMA4 : EPI3_PATH_POPC8;
+    return h->tuned_path ? h->tuned_path : EPI3_PATH_MMA4C;
 }
+int tune_handle(epi3_handle* h);
 
 // Candidate stage + result read-back shared by both scan forms.  Returns 1 to retry with a
 // larger candidate list, EPI3_OK, or an error.
@@ -519,7 +528,8 @@ int copy_out(epi3_handle* h, int32_t* out_trip, double* out_scores, int32_t* n_o
 
 // Register-split or plain form of the tensor scan for this handle (option "mma_form").
 bool mma_split(const epi3_handle* h, int kind) {
-    return h->mma_form == 0 ? mma_split_registers(h->N, kind) : h->mma_form == 2;
+    (void)kind;
+    return h->mma_form == 0 ? h->tuned_form == 2 : h->mma_form == 2;
 }
 
 CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k) {
@@ -627,31 +637,44 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
 // the handle's buffer; per range one compaction launch, then one scan launch over the range's
 // tiles (the candidate stage carries over from range to range).
 
-int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int top_k,
-                  int32_t* out_trip, double* out_scores, int32_t* n_out) {
+// The compaction plan of the pair range [pb, pe): per first SNP its chunks and tiles, grouped
+// into ranges whose chunks fit the handle's buffer; totals of compacted chunks and MMA K-steps
+// (the two work terms of this form, used by the tuner to extrapolate a slice's timing).
+struct CmpPlan {
+    std::vector<CmpFirst> firsts;
+    std::vector<int> range_start;   // first SNP of each range
+    std::vector<long long> range_chunks, range_tiles;
+    size_t need = 0;                // buffer bytes of the largest range
+    int i_hi = 0;                   // first SNPs [0, i_hi)
+    double chunks_total = 0.0, steps_total = 0.0;
+};
+
+void plan_cmp(const epi3_handle* h, long long pb, long long pe, CmpPlan& P) {
     const int M = h->M;
-    if (h->h_marg.empty()) {
-        h->h_marg.resize(2 * (size_t)M);
-        CK(cudaMemcpy(h->h_marg.data(), h->d_marg, sizeof(int2) * 2 * (size_t)M,
-                      cudaMemcpyDeviceToHost), "read marginals");
-    }
-    // first SNPs whose triplets can hold a pair of [pb, pe): every i below the last pair's j
-    int i_hi = M - 2;
-    if (pe > 0) {
-        const long long p = pe - 1;
+    // pair (i, j) has index j (j - 1) / 2 + i: the pairs of [pb, pe) have j in [j_lo, j_hi];
+    // first SNPs i < j_hi, each with the j blocks holding [j_lo, j_hi] (the epilogue drops
+    // the pairs outside the range at the ends)
+    auto second_of = [](long long p) {
         long long jj = (long long)((1.0 + std::sqrt(1.0 + 8.0 * (double)p)) * 0.5);
         while (jj * (jj - 1) / 2 > p) --jj;
         while ((jj + 1) * jj / 2 <= p) ++jj;
-        i_hi = (int)std::min<long long>(i_hi, jj);
-    }
-    std::vector<CmpFirst> firsts((size_t)std::max(i_hi, 0));
-    std::vector<int> range_start;   // first SNP of each range
-    std::vector<long long> range_chunks, range_tiles;
+        return jj;
+    };
+    const long long j_lo = second_of(pb), j_hi = pe > 0 ? second_of(pe - 1) : 0;
+    const int i_hi = std::max(0, (int)std::min<long long>(M - 2, j_hi));
+    P.i_hi = i_hi;
+    const int jb_first = (int)(j_lo / 64), jb_end = (int)(j_hi / 64) + 1;
+    std::vector<CmpFirst>& firsts = P.firsts;
+    std::vector<int>& range_start = P.range_start;
+    std::vector<long long>& range_chunks = P.range_chunks;
+    std::vector<long long>& range_tiles = P.range_tiles;
+    firsts.assign((size_t)i_hi, CmpFirst{});
     long long chunks = 0, tiles = 0;
-    size_t need = 0;
+    size_t& need = P.need;
     for (int i = 0; i < i_hi; ++i) {
         CmpFirst& f = firsts[i];
-        f.b_lo = (i + 1) / 64;
+        f.b_lo = std::max((i + 1) / 64, jb_first);
+        f.jb_end = jb_end;
         for (int c = 0; c < 2; ++c)
             for (int a = 0; a < 2; ++a) {
                 const int2 mg = h->h_marg[(size_t)c * M + i];
@@ -675,15 +698,36 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
             bq += nblk * f.ks[q];
         }
         chunks = bq;
-        f.tiles = cmp_tiles_of(M, f.b_lo);
+        f.tiles = cmp_tiles_of(M, f.b_lo, f.jb_end);
         f.tile0 = tiles;
         tiles += f.tiles;
+        P.chunks_total += (double)(bq - f.base[0]);
+        P.steps_total += (double)f.tiles * (f.ks[0] + f.ks[1] + f.ks[2] + f.ks[3]);
         need = std::max(need, (size_t)chunks * 16384);
     }
     if (!range_start.empty()) {
         range_chunks.push_back(chunks);
         range_tiles.push_back(tiles);
     }
+}
+
+int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int top_k,
+                  int32_t* out_trip, double* out_scores, int32_t* n_out) {
+    const int M = h->M;
+    if (h->h_marg.empty()) {
+        h->h_marg.resize(2 * (size_t)M);
+        CK(cudaMemcpy(h->h_marg.data(), h->d_marg, sizeof(int2) * 2 * (size_t)M,
+                      cudaMemcpyDeviceToHost), "read marginals");
+    }
+    CmpPlan P;
+    plan_cmp(h, pb, pe, P);
+    const std::vector<CmpFirst>& firsts = P.firsts;
+    const std::vector<int>& range_start = P.range_start;
+    const std::vector<long long>& range_tiles = P.range_tiles;
+    const int i_hi = P.i_hi;
+    const size_t need = P.need;
+    h->last_cmp_chunks = P.chunks_total;
+    h->last_cmp_steps = P.steps_total;
     if (h->cmp_bytes < need) {
         cudaFree(h->d_cmp);
         h->d_cmp = nullptr;
@@ -717,9 +761,10 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
         for (int r = 0; r < n_ranges; ++r) {
             const int i0 = range_start[r];
             const int n = (r + 1 < n_ranges ? range_start[r + 1] : i_hi) - i0;
-            if (h->profile) CK(cudaEventRecord(h->ev[4], h->stream), "event");
+            const bool time_cmp = h->profile || h->tuning;
+            if (time_cmp) CK(cudaEventRecord(h->ev[4], h->stream), "event");
             CK(launch_compact(h->pl, h->d_firsts + i0, i0, n, h->d_cmp, h->stream), "compaction launch");
-            if (h->profile) {  // profiling only: the host waits for each compaction to time it
+            if (time_cmp) {  // profiling and tuning only: the host waits for each compaction to time it
                 CK(cudaEventRecord(h->ev[5], h->stream), "event");
                 CK(cudaEventSynchronize(h->ev[5]), "compaction");
                 float ms = 0.f;
@@ -756,6 +801,7 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
     s.wait_producers_tmem = s.mma_issue = 0.f;
     s.compact_ms = compact_ms;
+    h->last_compact_ms = compact_ms;
     if (h->profile && h->d_prof) {
         unsigned long long p[8];
         CK(cudaMemcpy(p, h->d_prof, sizeof(p), cudaMemcpyDeviceToHost), "read profile");
@@ -793,6 +839,13 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     }
     if (n_out) *n_out = 0;
     if (top_k == 0) return EPI3_OK;
+    // measure the path (auto) or the tensor-scan form (form auto) once per shape bucket
+    if (!h->tuning && h->autotune &&
+        ((h->path == EPI3_PATH_AUTO && !h->tuned_path) ||
+         (is_mma_path(resolve_path(h)) && h->mma_form == 0 && h->tuned_form_path != resolve_path(h)))) {
+        const int rc = tune_handle(h);
+        if (rc != EPI3_OK) return rc;
+    }
     const int path = resolve_path(h);
     if (path != EPI3_PATH_POPC && path != EPI3_PATH_POPC8 && path != EPI3_PATH_MMA4C &&
         !is_mma_path(path))
@@ -1265,6 +1318,10 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
         else return fail(EPI3_ERR_ARG, "mma_form '%s' not auto, plain or split", value);
         return EPI3_OK;
     }
+    if (!strcmp(key, "autotune")) {
+        h->autotune = atoi(value) != 0;
+        return EPI3_OK;
+    }
     if (!strcmp(key, "timing")) {
         h->timing = atoi(value) != 0;
         return EPI3_OK;
@@ -1311,6 +1368,7 @@ struct epi3_batch {
     int4* d_tiles = nullptr;
     long long n_tiles = 0;
     bool split = false;                 // register-split form of the tensor scan
+    bool form_set = false;              // split measured on the first scan (or forced)
     double* d_scores = nullptr;         // [n][EPI3_MAX_TOPK]
     int* d_trip = nullptr;
     double* h_scores = nullptr;         // pinned
@@ -1352,10 +1410,13 @@ void batch_release(epi3_batch* b) {
 // scan kernels are timed on the cohort's heaviest pair slice (pairs with the smallest j,
 // about 1/16 of the pairs) and the lower kernel time per triplet wins.  Results are kept
 // per (M / 64, N / 1024) bucket for the process, and in the file named by EPI3_TUNE_CACHE
-// (lines "device<TAB>SMs<TAB>M/64<TAB>N/1024<TAB>path") across processes.
+// (lines "device<TAB>SMs<TAB>M/64<TAB>N/1024<TAB>path[<TAB>form<TAB>scope]") across
+// processes.  Scope 0 = a batch cohort's path, 1 = a handle's auto path and form, 2 = the
+// form of an explicitly chosen tensor path.
 struct TuneEntry {
     std::string dev;
     int sms, mb, nb, path;
+    int form = 0, scope = 0;
 };
 std::vector<TuneEntry> g_tune;
 bool g_tune_loaded = false;
@@ -1377,7 +1438,10 @@ void tune_load() {
     while (fgets(line, sizeof(line), fp)) {
         char name[256];
         TuneEntry e;
-        if (sscanf(line, "%255[^\t]\t%d\t%d\t%d\t%d", name, &e.sms, &e.mb, &e.nb, &e.path) == 5) {
+        const int got = sscanf(line, "%255[^\t]\t%d\t%d\t%d\t%d\t%d\t%d", name, &e.sms, &e.mb,
+                               &e.nb, &e.path, &e.form, &e.scope);
+        if (got == 5) e.form = e.scope = 0;
+        if (got == 5 || got == 7) {
             e.dev = name;
             g_tune.push_back(e);
         }
@@ -1391,8 +1455,114 @@ void tune_store(const TuneEntry& e) {
     if (!f) return;
     FILE* fp = fopen(f, "a");
     if (!fp) return;
-    fprintf(fp, "%s\t%d\t%d\t%d\t%d\n", e.dev.c_str(), e.sms, e.mb, e.nb, e.path);
+    fprintf(fp, "%s\t%d\t%d\t%d\t%d\t%d\t%d\n", e.dev.c_str(), e.sms, e.mb, e.nb, e.path, e.form,
+            e.scope);
     fclose(fp);
+}
+
+// The handle tuner: for path "auto", every scan form that supports the shape -- 8-cell POPC,
+// sample-compacted tensor, one-hot tensor in its plain and register-split forms -- is timed
+// on the heaviest pair slice (the first pairs, those with the smallest second SNP: at most 1/16
+// of the pairs and about 3e13 sample-triplets), after a warm-up on a sixteenth of it, and its
+// time is extrapolated to the whole scan by the form's work terms: triplets for the POPC and
+// one-hot forms; for the compacted form its compaction (timed apart, scaled by compacted
+// chunks) and its MMA K-steps, both from the plan of the whole scan.  The lowest wins.  For an explicitly chosen one-hot tensor path with form "auto", only its two forms
+// are timed.  Results are cached per bucket like the batch tuner's.
+int tune_handle(epi3_handle* h) {
+    const bool want_path = h->path == EPI3_PATH_AUTO;
+    const int fixed = want_path ? 0 : h->path;
+    struct Choice { int path, form; };
+    std::vector<Choice> cands;
+    if (want_path) {
+        cands.push_back({EPI3_PATH_POPC8, 0});
+        cands.push_back({EPI3_PATH_MMA4C, 0});
+        if (mma_tile_estimate(h->M) <= kMaxMmaTiles) {
+            cands.push_back({EPI3_PATH_MMA4, 1});
+            cands.push_back({EPI3_PATH_MMA4, 2});
+        }
+    } else {
+        cands.push_back({fixed, 1});
+        cands.push_back({fixed, 2});
+    }
+    const int scope = want_path ? 1 : 2;
+    tune_load();
+    const std::string dev = device_name(h->device);
+    const int mb = h->M / 64, nb = h->N / 1024;
+    for (const TuneEntry& e : g_tune)
+        if (e.dev == dev && e.sms == h->sm_count && e.mb == mb && e.nb == nb && e.scope == scope &&
+            (scope == 1 || e.path == fixed)) {
+            if (want_path) h->tuned_path = e.path;
+            if (e.form) {
+                h->tuned_form = e.form;
+                h->tuned_form_path = e.path;
+            }
+            return EPI3_OK;
+        }
+    const long long np = pairs(h->M - 1);
+    long long pe = std::max(1LL, np / 16);
+    while (pe > 1 && (double)triplets_in_pairs(h->M, 0, pe) * h->N > 3e13) pe /= 2;
+    const long long pw = std::max(1LL, pe / 16);
+    const double nt_full = (double)triplets_in_pairs(h->M, 0, np);
+    const double nt_slice = std::max(1.0, (double)triplets_in_pairs(h->M, 0, pe));
+    // the tuning scans run plain: no checksum slots, no profile counters
+    const int save_path = h->path, save_form = h->mma_form;
+    unsigned long long* const save_tsum = h->tsum;
+    const bool save_prof = h->profile;
+    h->tsum = nullptr;
+    h->profile = false;
+    h->tuning = true;
+    int32_t trip[3];
+    double sc;
+    int32_t nout = 0;
+    int best = -1, rc = EPI3_OK;
+    float best_ms = 0.f;
+    for (size_t q = 0; q < cands.size() && rc == EPI3_OK; ++q) {
+        h->path = cands[q].path;
+        h->mma_form = cands[q].form;
+        int r = scan_impl(h, 0, pw, 1, trip, &sc, &nout, false);
+        if (r == EPI3_OK) r = scan_impl(h, 0, pe, 1, trip, &sc, &nout, false);
+        if (r == EPI3_ERR_UNSUPPORTED) continue;  // this form does not serve the shape
+        if (r != EPI3_OK) {
+            rc = r;
+            break;
+        }
+        // the slice's time extrapolated to the whole scan by the form's own work terms
+        float ms = h->stats.scan_kernel_ms * (float)(nt_full / nt_slice);
+        if (cands[q].path == EPI3_PATH_MMA4C && h->last_cmp_chunks > 0.0 && h->last_cmp_steps > 0.0) {
+            CmpPlan full;
+            plan_cmp(h, 0, np, full);
+            const float t_cmp = std::min(h->last_compact_ms, h->stats.scan_kernel_ms);
+            ms = t_cmp * (float)(full.chunks_total / h->last_cmp_chunks) +
+                 (h->stats.scan_kernel_ms - t_cmp) * (float)(full.steps_total / h->last_cmp_steps);
+        }
+        if (best < 0 || ms < best_ms) {
+            best = (int)q;
+            best_ms = ms;
+        }
+    }
+    h->path = save_path;
+    h->mma_form = save_form;
+    h->tsum = save_tsum;
+    h->profile = save_prof;
+    h->tuning = false;
+    if (rc != EPI3_OK) return rc;
+    if (best < 0) return fail(EPI3_ERR_UNSUPPORTED, "no scan form serves %d SNPs", h->M);
+    const Choice c = cands[(size_t)best];
+    if (want_path) h->tuned_path = c.path;
+    if (c.form) {
+        h->tuned_form = c.form;
+        h->tuned_form_path = c.path;
+    }
+    TuneEntry e;
+    e.dev = dev;
+    e.sms = h->sm_count;
+    e.mb = mb;
+    e.nb = nb;
+    e.path = c.path;
+    e.form = c.form;
+    e.scope = scope;
+    tune_store(e);
+    return EPI3_OK;
 }
 
 int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
@@ -1411,7 +1581,7 @@ int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
     const int mb = h->M / 64, nb = h->N / 1024;
     for (const TuneEntry& e : g_tune)
         if (e.dev == dev && e.sms == b->sm_count && e.mb == mb && e.nb == nb &&
-            (e.path == EPI3_PATH_MMA4 || e.path == EPI3_PATH_POPC8)) {
+            e.scope == 0 && (e.path == EPI3_PATH_MMA4 || e.path == EPI3_PATH_POPC8)) {
             *path_out = e.path;
             return EPI3_OK;
         }
@@ -1611,20 +1781,21 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
         if ((rc = ensure_pair_tables(h)) != EPI3_OK) return bail(rc);
     }
     std::vector<int4> tiles;
-    double tile_samples = 0.0;          // sum over the tiles of their data set's samples
     for (int c = 0; c < n_cohorts; ++c) {
         epi3_handle* h = b->h[c];
         if ((rc = tune_path(b, h, &b->path[c], &b->tune_ms)) != EPI3_OK) return bail(rc);
         if (b->path[c] == EPI3_PATH_MMA4) {
             if ((rc = ensure_onehot(h, kKindE2M1)) != EPI3_OK) return bail(rc);
-            const size_t before = tiles.size();
             append_tiles(h->M, 0, pairs(h->M - 1), c, tiles);
-            tile_samples += (double)(tiles.size() - before) * h->N;
         }
         h->path = b->path[c];
     }
     b->n_tiles = (long long)tiles.size();
-    b->split = !tiles.empty() && mma_split_registers(tile_samples / (double)tiles.size(), kKindE2M1);
+    // the tensor launch's form (plain or register-split) is measured on the first scan, unless
+    // EPI3_BATCH_FORM forces one
+    const char* form = getenv("EPI3_BATCH_FORM");
+    b->split = form && !strcmp(form, "split");
+    b->form_set = tiles.empty() || (form && (!strcmp(form, "split") || !strcmp(form, "plain")));
     if ((e = dev_alloc((void**)&b->d_tiles, sizeof(int4) * (tiles.empty() ? 1 : tiles.size()))) != cudaSuccess)
         return bail(cuda_fail(e, "alloc tiles"));
     if (!tiles.empty() &&
@@ -1652,6 +1823,23 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
         const long long m = b->h[c]->M;
         if (top_k > m * (m - 1) * (m - 2) / 6)
             return fail(EPI3_ERR_ARG, "top_k %d exceeds the triplets of cohort %d", top_k, c);
+    }
+    if (!b->form_set) {
+        // first scan: replay the batch once in each form of the tensor launch (both give the
+        // full result) and keep the faster
+        b->form_set = true;
+        float t[2] = {0.f, 0.f};
+        for (int f = 0; f < 2; ++f) {
+            b->split = f == 1;
+            b->graph_k = -1;  // capture again with this form
+            const int rc = epi3_batch_scan(b, top_k, out_triplets, out_scores);
+            if (rc != EPI3_OK) return rc;
+            cudaEventElapsedTime(&t[f], b->ev[0], b->ev[4]);
+        }
+        const bool split = t[1] < t[0];
+        if (split == b->split) return EPI3_OK;  // the last replay's result stands
+        b->split = split;
+        b->graph_k = -1;
     }
     for (int attempt = 0;; ++attempt) {
         if (!b->exec || b->graph_k != top_k) {
@@ -1747,6 +1935,13 @@ int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out) {
 int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths) {
     if (!b || !out_paths) return fail(EPI3_ERR_ARG, "null argument");
     for (int c = 0; c < b->n; ++c) out_paths[c] = b->path[c];
+    return EPI3_OK;
+}
+
+int epi3_batch_get_forms(const epi3_batch* b, int32_t* out_forms) {
+    if (!b || !out_forms) return fail(EPI3_ERR_ARG, "null argument");
+    for (int c = 0; c < b->n; ++c)
+        out_forms[c] = b->path[c] != EPI3_PATH_MMA4 ? 0 : !b->form_set ? -1 : b->split ? 2 : 1;
     return EPI3_OK;
 }
 

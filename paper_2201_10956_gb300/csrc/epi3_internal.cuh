@@ -185,8 +185,9 @@ constexpr int kCmpSets = 4;      // (class, genotype 0/1 of the first SNP)
 struct CmpFirst {
     long long base[kCmpSets];
     int ks[kCmpSets];
-    int b_lo;                    // first 64-SNP block holding an SNP after i
+    int b_lo;                    // first 64-SNP block compacted: the first j block of the tiles
     int tiles;                   // tiles of this first SNP
+    int jb_end;                  // one past its last j block (the pair range's last j)
     long long tile0;             // index of its first tile in the range
 };
 
@@ -203,7 +204,7 @@ inline long long cmp_chunks_of(const CmpFirst& f, int M) {
     const long long nblk = (M + 63) / 64 - f.b_lo;
     return nblk * ((long long)f.ks[0] + f.ks[1] + f.ks[2] + f.ks[3]);
 }
-int cmp_tiles_of(int M, int b_lo);            // tiles (64 j x 32 k) of one first SNP
+int cmp_tiles_of(int M, int b_lo, int jb_end); // tiles (64 j x 32 k) of one first SNP
 size_t scan_cmp_smem();
 // compaction of first SNPs i0 .. i0 + n_first - 1 into cmp (chunk indices from firsts)
 cudaError_t launch_compact(const Planes& pl, const CmpFirst* firsts, int i0, int n_first,
@@ -211,13 +212,12 @@ cudaError_t launch_compact(const Planes& pl, const CmpFirst* firsts, int i0, int
 cudaError_t launch_scan_cmp(const CmpArgs& a, int grid, cudaStream_t st, bool checksum);
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
-// split: the register-split form of the kernel (mma_split_registers of the launch's samples
-// per data set, for a batch their mean weighted by tiles)
+// split: the register-split form of the kernel (measured per shape by the handle tuner, per
+// batch by timing both forms on its first scan)
 // checksum: the cohorts' tsum slots are set (the instrumented instantiation adds every table)
 cudaError_t launch_scan_mma(const CohortDev* cohorts, const int4* tiles, long long n_tiles,
                             int kind, int grid, cudaStream_t st, unsigned long long* prof,
                             bool split, bool checksum = false);
-bool mma_split_registers(double samples, int kind);
 int mma_threads(bool split);   // threads per CTA of the tensor-core scan
 cudaError_t scan_popc8_occupancy(int block, size_t smem, int* ctas_per_sm);
 

@@ -30,6 +30,7 @@
 // tensor-memory lane quadrant); registers move from the first warp group to the epilogue
 // (setmaxnreg).  Every mbarrier wait is bounded; on timeout the kernel
 // records kStTimeout, waits for its own copies and MMAs, frees tensor memory and returns.
+#include <algorithm>
 #include <atomic>
 
 #include "epi3_internal.cuh"
@@ -77,36 +78,46 @@ __device__ __forceinline__ void cmp_push(uint8_t* set_base, int row, CmpStream& 
     }
 }
 
+// Push the set-a bits of one 32-sample word: compress by the set's mask (Hacker's Delight 7-4,
+// masks prepared once per word by cmp_masks), append to the stream, emit each full word.
+__device__ __forceinline__ void cmp_word(uint8_t* set_base, int row, CmpStream& st, uint32_t x,
+                                         uint32_t mask, const uint32_t* mv, int n) {
+    if (n == 0) return;
+    cmp_push(set_base, row, st, n == 32 ? x : cmp_bits(x, mask, mv), n);
+}
+
 // CTA (b, i - i0, c), 128 threads: thread r writes row r = 2 (m - 64 b) + z of every chunk of
 // block b for the two sets (c, 0) and (c, 1) of first SNP i: the bits [g_m = z] of the class-c
 // samples with g_i = a, in sample order, then the bias sample, then zeros to the set's K-steps.
+// Plane words come four at a time (one 16-byte load per 128 samples, the next one in flight
+// while the current one is compressed).
 __global__ void __launch_bounds__(128)
 compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* __restrict__ cmp) {
     __shared__ uint32_t s_mask[2][kMaskWords];
     __shared__ uint32_t s_mv[2][kMaskWords][5];
     __shared__ int s_pop[2][kMaskWords];
     const int b = blockIdx.x, i = i0 + (int)blockIdx.y, c = (int)blockIdx.z;
-    const CmpFirst f = firsts[blockIdx.y];
-    if (b < f.b_lo) return;  // whole CTA: no block before the first SNP's successors
+    // the fields this CTA needs, read in place (a local copy indexed by the class would live in
+    // local memory)
+    const CmpFirst* const fp = firsts + blockIdx.y;
+    const int b_lo = fp->b_lo;
+    if (b < b_lo) return;  // whole CTA: no block before the first SNP's successors
+    const int ks0 = fp->ks[2 * c], ks1 = fp->ks[2 * c + 1];
+    const long long fb0 = fp->base[2 * c], fb1 = fp->base[2 * c + 1];
     const int M = pl.M;
     const int r = threadIdx.x, z = r & 1;
     const int m = 64 * b + (r >> 1);
     const long long coff = c ? pl.coff[1] : pl.coff[0];
     const int W4 = c ? pl.W4[1] : pl.W4[0];
     const int W = 4 * W4;                       // 32-sample words of the class
-    uint8_t* base[2];
-    CmpStream st[2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int q = 2 * c + a;
-        base[a] = cmp + (size_t)(f.base[q] + (long long)(b - f.b_lo) * f.ks[q]) * kCmpChunk;
-        st[a].acc = 0ull;
-        st[a].fill = 0;
-        st[a].word = 0;
-    }
-    const uint32_t* prow = reinterpret_cast<const uint32_t*>(pl.planes + coff);
+    uint8_t* const base0 = cmp + (size_t)(fb0 + (long long)(b - b_lo) * ks0) * kCmpChunk;
+    uint8_t* const base1 = cmp + (size_t)(fb1 + (long long)(b - b_lo) * ks1) * kCmpChunk;
+    CmpStream st0{0ull, 0, 0}, st1{0ull, 0, 0};
+    const uint4* const pc = pl.planes + coff;   // [plane][group][SNP] of 4 words
+    const uint32_t* const prow = reinterpret_cast<const uint32_t*>(pc);
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     for (int w0 = 0; w0 < W; w0 += kMaskWords) {
-        const int nw = min(kMaskWords, W - w0);
+        const int nw = min(kMaskWords, W - w0);   // a multiple of 4
         __syncthreads();  // the previous pass's masks are no longer read
         for (int t = threadIdx.x; t < 2 * nw; t += blockDim.x) {
             const int a = t / nw, w = w0 + t % nw;
@@ -117,27 +128,31 @@ compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* 
             cmp_masks(mk, s_mv[a][w - w0]);
         }
         __syncthreads();
-        for (int w = 0; w < nw; ++w) {
-            const int ww = w0 + w;
-            const uint32_t v = m < M ? prow[((size_t)(z * W4 + (ww >> 2)) * M + m) * 4 + (ww & 3)] : 0u;
+        const int g0 = w0 >> 2, ng = nw >> 2;
+        const uint4* const src = pc + (size_t)(z * W4 + g0) * M + m;
+        uint4 vn = m < M ? __ldg(src) : zero4;
+        for (int g = 0; g < ng; ++g) {
+            const uint4 v = vn;
+            if (g + 1 < ng) vn = m < M ? __ldg(src + (size_t)(g + 1) * M) : zero4;
+            const uint32_t xs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int n = s_pop[a][w];
-                if (n == 0) continue;  // uniform: the masks are the CTA's
-                const uint32_t bits = cmp_bits(v, s_mask[a][w], s_mv[a][w]);
-                cmp_push(base[a], r, st[a], bits, n);
+            for (int e = 0; e < 4; ++e) {
+                const int w = 4 * g + e;
+                cmp_word(base0, r, st0, xs[e], s_mask[0][w], s_mv[0][w], s_pop[0][w]);
+                cmp_word(base1, r, st1, xs[e], s_mask[1][w], s_mv[1][w], s_pop[1][w]);
             }
         }
     }
     // the bias sample, then zeros up to the set's K-steps (8 words each)
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int words = 8 * f.ks[2 * c + a];
-        cmp_push(base[a], r, st[a], 1u, 1);
-        while (st[a].word < words) {
-            cmp_emit(base[a], r, st[a], (uint32_t)st[a].acc);
-            st[a].acc >>= 32;
-        }
+    cmp_push(base0, r, st0, 1u, 1);
+    for (const int words = 8 * ks0; st0.word < words;) {
+        cmp_emit(base0, r, st0, (uint32_t)st0.acc);
+        st0.acc >>= 32;
+    }
+    cmp_push(base1, r, st1, 1u, 1);
+    for (const int words = 8 * ks1; st1.word < words;) {
+        cmp_emit(base1, r, st1, (uint32_t)st1.acc);
+        st1.acc >>= 32;
     }
 }
 
@@ -193,7 +208,8 @@ struct CmpTile {
     int jb, kb;                  // 64-SNP block of j, 32-SNP block of k
 };
 
-// Tile t of the range: first SNPs in order, then j blocks from b_lo, then k blocks from 2 jb.
+// Tile t of the range: first SNPs in order, then j blocks from b_lo (to jb_end), then k blocks
+// from 2 jb.
 __device__ __forceinline__ CmpTile cmp_tile(const CmpArgs& a, long long t) {
     int lo = 0, hi = a.n_first;  // last f with tile0 <= t
     while (hi - lo > 1) {
@@ -590,8 +606,8 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
 
 size_t scan_cmp_smem() { return 1024 + kSlots * (kSlotA + kSlotB) + 256 + sizeof(EpiShared) + 64; }
 
-int cmp_tiles_of(int M, int b_lo) {
-    const int nb = (M + 63) / 64, nk = (M + kTK - 1) / kTK;
+int cmp_tiles_of(int M, int b_lo, int jb_end) {
+    const int nb = std::min((M + 63) / 64, jb_end), nk = (M + kTK - 1) / kTK;
     int t = 0;
     for (int jb = b_lo; jb < nb; ++jb) t += nk - 2 * jb;
     return t;

@@ -74,9 +74,6 @@ __host__ __device__ constexpr int epi_warp0() { return kSplit ? 8 : 2; }
 constexpr int kRegLaunch = 128, kRegCtl = 56, kRegProd = 104, kRegEpi = 176;
 static_assert(kRegCtl + kRegProd + 2 * kRegEpi == 4 * kRegLaunch, "register split");
 static_assert(threads_of<true>() * kRegLaunch == 65536, "the split launch holds the whole register file");
-// the split form for data sets with fewer samples than this in E2M1 (measured crossover: the
-// split is 7 % faster at 8192 samples and 1.4 % slower at 16384)
-constexpr double kSplitBelow = 14336.0;
 constexpr int kYChunk = kChunk / 2;      // one-hot rows (j, b) of 32 second SNPs: 64 rows
 constexpr int kXBytes = 256;             // one-hot rows (i, 0) and (i, 1): 2 rows
 constexpr int kTmemCols = 512;
@@ -963,10 +960,6 @@ static cudaError_t launch_kind(const CohortDev* cohorts, const int4* tiles, long
                       : launch_variant<kKind, false, false>(cohorts, tiles, n_tiles, grid, st, prof);
 }
 
-bool mma_split_registers(double samples, int kind) {
-    // the crossover scales with the MMA time per sample: 2x (E4M3) and 4x (FP16) that of E2M1
-    return samples * (256.0 / mma_samples_per_step(kind)) < kSplitBelow;
-}
 
 int mma_threads(bool split) { return split ? threads_of<true>() : threads_of<false>(); }
 

@@ -30,7 +30,8 @@ SYMBOLS = ("epi3_create", "epi3_scan", "epi3_scan_range", "epi3_scan_pairs", "ep
            "epi3_last_error",
            "epi3_tables", "epi3_scores", "epi3_set_option", "epi3_get_stats", "epi3_get_shape",
            "epi3_scan_noalloc", "epi3_scan_scores", "epi3_scan_checksum", "epi3_batch_create", "epi3_batch_scan",
-           "epi3_batch_destroy", "epi3_batch_get_stats", "epi3_batch_get_paths", "epi3_scan_batch")
+           "epi3_batch_destroy", "epi3_batch_get_stats", "epi3_batch_get_paths", "epi3_batch_get_forms",
+           "epi3_scan_batch")
 
 
 class Epi3Error(RuntimeError):
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         "epi3_batch_destroy": [P],
         "epi3_batch_get_stats": [P, ctypes.POINTER(Stats)],
         "epi3_batch_get_paths": [P, P],
+        "epi3_batch_get_forms": [P, P],
         "epi3_scan_batch": [I32, P, I32, P, P, I32, P],
     }
     for name, args in sig.items():
@@ -335,6 +337,12 @@ class Batch:
     def paths(self):
         out = np.empty(self.n, dtype=np.int32)
         _check(load().epi3_batch_get_paths(self._b, _ptr(out)))
+        return out
+
+    def forms(self):
+        """Per cohort: 0 not a tensor cohort, 1 plain, 2 register-split, -1 not measured yet."""
+        out = np.empty(self.n, dtype=np.int32)
+        _check(load().epi3_batch_get_forms(self._b, _ptr(out)))
         return out
 
 
