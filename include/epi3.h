@@ -249,8 +249,8 @@ typedef struct {
        skipped without its exact FP32 score; the bound comes from the approximation's error
        measured on the device for every count 0..N+1 */
     float k2_prune_bound;
-    /* sample-compacted form (EPI3_PATH_MMA4C) with option "profile" = 1: device time of the
-       compaction kernels, a part of scan_kernel_ms (0 otherwise) */
+    /* sample-compacted form (EPI3_PATH_MMA4C): device time of the compaction kernels, a part
+       of scan_kernel_ms (0 for the other forms) */
     float compact_ms;
 } epi3_stats;
 

@@ -115,6 +115,7 @@ struct epi3_handle {
     // last compacted-form scan: its plan's work terms and (tuning scans) compaction time
     double last_cmp_chunks = 0.0, last_cmp_steps = 0.0;
     float last_compact_ms = 0.f;
+    std::vector<cudaEvent_t> cmp_ev;     // event pairs around the compaction launches
     unsigned long long* d_prof = nullptr;
     uint8_t* d_cmp = nullptr;     // compacted chunks of the sample-compacted tensor form
     size_t cmp_bytes = 0;
@@ -130,8 +131,8 @@ struct epi3_handle {
     int threads = 128;
     int ctas_per_sm = 0;
     bool timing = false;
-    // scan start, kernels start, kernels end, scan end; 4-5 bracket each compaction (profile)
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // scan start, kernels start, kernels end, scan end
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     epi3_stats stats{};
 };
 
@@ -164,6 +165,7 @@ void release(epi3_handle* h) {
     cudaFreeHost(h->h_trip);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : h->cmp_ev) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -745,6 +747,11 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
     const int grid = h->sm_count;
     const int n_ranges = (int)range_start.size();
     float compact_ms = 0.f;
+    while (h->cmp_ev.size() < 2 * (size_t)n_ranges) {  // one event pair per compaction launch
+        cudaEvent_t e = nullptr;
+        CK(cudaEventCreate(&e), "event create");
+        h->cmp_ev.push_back(e);
+    }
     for (int attempt = 0;; ++attempt) {
         if (inject("launch")) return fail(EPI3_ERR_CUDA, "injected launch failure");
         CK(cudaEventRecord(h->ev[0], h->stream), "event");
@@ -761,16 +768,9 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
         for (int r = 0; r < n_ranges; ++r) {
             const int i0 = range_start[r];
             const int n = (r + 1 < n_ranges ? range_start[r + 1] : i_hi) - i0;
-            const bool time_cmp = h->profile || h->tuning;
-            if (time_cmp) CK(cudaEventRecord(h->ev[4], h->stream), "event");
+            CK(cudaEventRecord(h->cmp_ev[2 * r], h->stream), "event");
             CK(launch_compact(h->pl, h->d_firsts + i0, i0, n, h->d_cmp, h->stream), "compaction launch");
-            if (time_cmp) {  // profiling and tuning only: the host waits for each compaction to time it
-                CK(cudaEventRecord(h->ev[5], h->stream), "event");
-                CK(cudaEventSynchronize(h->ev[5]), "compaction");
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]);
-                compact_ms += ms;
-            }
+            CK(cudaEventRecord(h->cmp_ev[2 * r + 1], h->stream), "event");
             CmpArgs a{};
             a.cd = cohort_of(h, pb, pe, top_k);
             a.firsts = h->d_firsts + i0;
@@ -787,6 +787,11 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
         if (rc == 1) continue;
         if (rc != EPI3_OK) return rc;
         break;
+    }
+    for (int r = 0; r < n_ranges; ++r) {  // finish_scan synchronised the stream
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->cmp_ev[2 * r], h->cmp_ev[2 * r + 1]);
+        compact_ms += ms;
     }
     const int rc = copy_out(h, out_trip, out_scores, n_out);
     if (rc != EPI3_OK) return rc;
