@@ -209,6 +209,8 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
  * the process and appended to the file named by the environment variable EPI3_TUNE_CACHE,
  * if set, for later processes) | "popc" | "popc8" | "mma" | "mma16" | "mma4" | "mma4c";
  * "autotune" = "1" (default) | "0" (no measuring: auto = EPI3_PATH_MMA4C, form plain);
+ * "candidates" = initial length of the FP32 candidate list (64 .. 2^28; default 2^20 from
+ * 2^26 triplets on, else 2^16; a scan that overflows it grows it 8x and runs again);
  * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
  * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);
  * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with

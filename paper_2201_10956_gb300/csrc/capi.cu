@@ -309,7 +309,10 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     cleanup();
     if (rc != EPI3_OK) return rc;
     if ((rc = build_k2_tables(h)) != EPI3_OK) return rc;
-    h->cand_cap = inject("cand") ? 128 : 1LL << 16;
+    // FP32 candidate list: the CTAs flush their in-band candidates before the shared threshold
+    // tightens, about 10^5 of them on a large scan (a list that overflows costs a whole rescan)
+    const long long m = h->M;
+    h->cand_cap = inject("cand") ? 128 : m * (m - 1) * (m - 2) / 6 >= (1LL << 26) ? 1LL << 20 : 1LL << 16;
     CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "alloc candidates");
     CK(dev_alloc((void**)&h->d_fin, sizeof(Final) * kFinalCap), "alloc final");
     CK(dev_alloc((void**)&h->d_out_scores, sizeof(double) * EPI3_MAX_TOPK), "alloc out scores");
@@ -1323,6 +1326,15 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
         else return fail(EPI3_ERR_ARG, "mma_form '%s' not auto, plain or split", value);
         return EPI3_OK;
     }
+    if (!strcmp(key, "candidates")) {
+        const long long n = atoll(value);
+        if (n < 64 || n > (1LL << 28)) return fail(EPI3_ERR_ARG, "candidates %s outside 64..2^28", value);
+        cudaFree(h->d_cand);
+        h->d_cand = nullptr;
+        h->cand_cap = n;
+        CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "alloc candidates");
+        return EPI3_OK;
+    }
     if (!strcmp(key, "autotune")) {
         h->autotune = atoi(value) != 0;
         return EPI3_OK;
@@ -1516,16 +1528,16 @@ int tune_handle(epi3_handle* h) {
     h->tsum = nullptr;
     h->profile = false;
     h->tuning = true;
-    int32_t trip[3];
-    double sc;
+    int32_t trip[3 * 10];   // top-10, the usual request: a list sized like a real scan's
+    double sc[10];
     int32_t nout = 0;
     int best = -1, rc = EPI3_OK;
     float best_ms = 0.f;
     for (size_t q = 0; q < cands.size() && rc == EPI3_OK; ++q) {
         h->path = cands[q].path;
         h->mma_form = cands[q].form;
-        int r = scan_impl(h, 0, pw, 1, trip, &sc, &nout, false);
-        if (r == EPI3_OK) r = scan_impl(h, 0, pe, 1, trip, &sc, &nout, false);
+        int r = scan_impl(h, 0, pw, 10, trip, sc, &nout, false);
+        if (r == EPI3_OK) r = scan_impl(h, 0, pe, 10, trip, sc, &nout, false);
         if (r == EPI3_ERR_UNSUPPORTED) continue;  // this form does not serve the shape
         if (r != EPI3_OK) {
             rc = r;
