@@ -48,6 +48,8 @@ L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
 # an entry is removed whenever that kernel changes.
 TRAFFIC = {
     ("mma4", "large"): 567.59e6 + 7.07e6,   # scan_mma_kernel<e2m1> (plain form), 2048 x 16384
+    # scan_cmp_kernel, 2048 x 16384, 2 GiB ranges: mean DRAM read + write of two launches
+    ("mma4c", "large"): (5366121216 + 7884800 + 4828321536 + 1882880) / 2,
 }
 
 
@@ -384,6 +386,8 @@ def run_ours(args, rank, world, local_rank):
             pack_ms.append(hp.stats()["pack_ms"])
     h = epi.Handle(g_dev, p_dev, stream=stream)
     h.set_option("path", args.path)
+    if args.cmp_buffer_mb:
+        h.set_option("cmp_buffer_mb", str(args.cmp_buffer_mb))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
     def step():
@@ -515,6 +519,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--snps", type=int, default=None,
                     help="another SNP count for the workload (a smaller case for profiling)")
+    ap.add_argument("--cmp-buffer-mb", type=int, default=None,
+                    help="device memory for the compacted chunks of path mma4c (option cmp_buffer_mb)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
