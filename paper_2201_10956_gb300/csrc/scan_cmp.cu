@@ -42,7 +42,8 @@ namespace epi3 {
 namespace {
 
 constexpr int kCmpChunk = 16384;         // one compacted chunk: 128 rows (m, z) x 256 samples
-constexpr int kMaskWords = 256;          // selection words staged per pass of the compaction
+constexpr int kMaskWords = 128;          // selection words staged per pass of the compaction
+constexpr int kSlabBytes = 32 * 128;     // one warp's 32 rows of a chunk: 4 KB, contiguous
 
 }  // namespace
 
@@ -56,46 +57,71 @@ struct CmpStream {
     int word;                   // words written
 };
 
-__device__ __forceinline__ void cmp_emit(uint8_t* set_base, int row, CmpStream& st, uint32_t w) {
-    uint8_t* chunk = set_base + (size_t)(st.word >> 3) * kCmpChunk;
+// A word goes to the warp's shared-memory image of its 32 rows of the current chunk (the same
+// 128B-swizzled layout); when the K-step's eighth word is in, the warp writes the 4 KB slab out
+// with contiguous 16-byte stores (every thread of the CTA emits at the same points: the bit
+// counts per word are the CTA's).
+__device__ __forceinline__ void cmp_emit(uint8_t* set_base, uint8_t* slab, int row, CmpStream& st,
+                                         uint32_t w) {
     uint4 v;
     v.x = byte_to_e2m1(w);
     v.y = byte_to_e2m1(w >> 8);
     v.z = byte_to_e2m1(w >> 16);
     v.w = byte_to_e2m1(w >> 24);
-    *reinterpret_cast<uint4*>(chunk + sw128_off((uint32_t)row, (uint32_t)(st.word & 7))) = v;
+    const uint32_t u = (uint32_t)(st.word & 7);
+    *reinterpret_cast<uint4*>(slab + sw128_off((uint32_t)(row & 31), u)) = v;
+    if (u == 7) {  // uniform across the warp
+        __syncwarp();
+        uint8_t* const dst = set_base + (size_t)(st.word >> 3) * kCmpChunk + (size_t)(row & ~31) * 128;
+        const int lane = row & 31;
+#pragma unroll
+        for (int j = 0; j < kSlabBytes / 512; ++j) {
+            const int off = 16 * (lane + 32 * j);
+            *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(slab + off);
+        }
+        __syncwarp();
+    }
     ++st.word;
 }
 
-__device__ __forceinline__ void cmp_push(uint8_t* set_base, int row, CmpStream& st, uint32_t bits,
-                                         int n) {
+__device__ __forceinline__ void cmp_push(uint8_t* set_base, uint8_t* slab, int row, CmpStream& st,
+                                         uint32_t bits, int n) {
     st.acc |= (unsigned long long)bits << st.fill;
     st.fill += n;
     if (st.fill >= 32) {
-        cmp_emit(set_base, row, st, (uint32_t)st.acc);
+        cmp_emit(set_base, slab, row, st, (uint32_t)st.acc);
         st.acc >>= 32;
         st.fill -= 32;
     }
 }
 
-// Push the set-a bits of one 32-sample word: compress by the set's mask (Hacker's Delight 7-4,
-// masks prepared once per word by cmp_masks), append to the stream, emit each full word.
-__device__ __forceinline__ void cmp_word(uint8_t* set_base, int row, CmpStream& st, uint32_t x,
-                                         uint32_t mask, const uint32_t* mv, int n) {
+constexpr int kCompactThreads = 128;     // one row (SNP, genotype) of the 64-SNP block per thread
+
+// Push the bits of one 32-sample word selected by a set's mask: compress by the mask (Hacker's
+// Delight 7-4, masks prepared once per word by cmp_masks), append to the stream, emit each full
+// word.
+__device__ __forceinline__ void cmp_word(uint8_t* set_base, uint8_t* slab, int row, CmpStream& st,
+                                         uint32_t x, uint32_t mask, const uint32_t* mv, int n) {
     if (n == 0) return;
-    cmp_push(set_base, row, st, n == 32 ? x : cmp_bits(x, mask, mv), n);
+    cmp_push(set_base, slab, row, st, n == 32 ? x : cmp_bits(x, mask, mv), n);
 }
+
+// One selection word's masks for both sets, read with four 16-byte shared-memory loads:
+// {mask0, mask1, pop0, pop1}, mv0[0..3], mv1[0..3], {mv0[4], mv1[4], -, -}.
+struct MaskWord {
+    uint4 q[4];
+};
 
 // CTA (b, i - i0, c), 128 threads: thread r writes row r = 2 (m - 64 b) + z of every chunk of
 // block b for the two sets (c, 0) and (c, 1) of first SNP i: the bits [g_m = z] of the class-c
 // samples with g_i = a, in sample order, then the bias sample, then zeros to the set's K-steps.
 // Plane words come four at a time (one 16-byte load per 128 samples, the next one in flight
-// while the current one is compressed).
-__global__ void __launch_bounds__(128)
+// while the current one is compressed); each word's masks of both sets come in four 16-byte
+// shared-memory loads.
+__global__ void __launch_bounds__(kCompactThreads)
 compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* __restrict__ cmp) {
-    __shared__ uint32_t s_mask[2][kMaskWords];
-    __shared__ uint32_t s_mv[2][kMaskWords][5];
-    __shared__ int s_pop[2][kMaskWords];
+    __shared__ MaskWord s_w[kMaskWords];
+    __shared__ __align__(128) uint8_t s_slab[2][kCompactThreads / 32][kSlabBytes];
     const int b = blockIdx.x, i = i0 + (int)blockIdx.y, c = (int)blockIdx.z;
     // the fields this CTA needs, read in place (a local copy indexed by the class would live in
     // local memory)
@@ -112,24 +138,33 @@ compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* 
     const int W = 4 * W4;                       // 32-sample words of the class
     uint8_t* const base0 = cmp + (size_t)(fb0 + (long long)(b - b_lo) * ks0) * kCmpChunk;
     uint8_t* const base1 = cmp + (size_t)(fb1 + (long long)(b - b_lo) * ks1) * kCmpChunk;
-    CmpStream st0{0ull, 0, 0}, st1{0ull, 0, 0};
+    CmpStream s0{0ull, 0, 0}, s1{0ull, 0, 0};   // sets (c, 0) and (c, 1)
+    uint8_t* const slab0 = s_slab[0][r >> 5];
+    uint8_t* const slab1 = s_slab[1][r >> 5];
     const uint4* const pc = pl.planes + coff;   // [plane][group][SNP] of 4 words
     const uint32_t* const prow = reinterpret_cast<const uint32_t*>(pc);
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     for (int w0 = 0; w0 < W; w0 += kMaskWords) {
         const int nw = min(kMaskWords, W - w0);   // a multiple of 4
         __syncthreads();  // the previous pass's masks are no longer read
-        for (int t = threadIdx.x; t < 2 * nw; t += blockDim.x) {
-            const int a = t / nw, w = w0 + t % nw;
-            // word w of plane a of SNP i: group w / 4, word w % 4
-            const uint32_t mk = prow[((size_t)(a * W4 + (w >> 2)) * M + i) * 4 + (w & 3)];
-            s_mask[a][w - w0] = mk;
-            s_pop[a][w - w0] = __popc(mk);
-            cmp_masks(mk, s_mv[a][w - w0]);
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+            // word w0 + w of planes 0 and 1 of SNP i: group (w0 + w) / 4, word (w0 + w) % 4
+            const int ww = w0 + w;
+            const uint32_t mk0 = prow[((size_t)(ww >> 2) * M + i) * 4 + (ww & 3)];
+            const uint32_t mk1 = prow[((size_t)(W4 + (ww >> 2)) * M + i) * 4 + (ww & 3)];
+            uint32_t v0[5], v1[5];
+            cmp_masks(mk0, v0);
+            cmp_masks(mk1, v1);
+            MaskWord e;
+            e.q[0] = make_uint4(mk0, mk1, (uint32_t)__popc(mk0), (uint32_t)__popc(mk1));
+            e.q[1] = make_uint4(v0[0], v0[1], v0[2], v0[3]);
+            e.q[2] = make_uint4(v1[0], v1[1], v1[2], v1[3]);
+            e.q[3] = make_uint4(v0[4], v1[4], 0u, 0u);
+            s_w[w] = e;
         }
         __syncthreads();
         const int g0 = w0 >> 2, ng = nw >> 2;
-        const uint4* const src = pc + (size_t)(z * W4 + g0) * M + m;
+        const uint4* const src = pc + (size_t)(z * W4 + g0) * M + m;   // this row's plane
         uint4 vn = m < M ? __ldg(src) : zero4;
         for (int g = 0; g < ng; ++g) {
             const uint4 v = vn;
@@ -137,22 +172,25 @@ compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* 
             const uint32_t xs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int w = 4 * g + e;
-                cmp_word(base0, r, st0, xs[e], s_mask[0][w], s_mv[0][w], s_pop[0][w]);
-                cmp_word(base1, r, st1, xs[e], s_mask[1][w], s_mv[1][w], s_pop[1][w]);
+                const MaskWord& mw = s_w[4 * g + e];
+                const uint4 h = mw.q[0], a0 = mw.q[1], a1 = mw.q[2], a4 = mw.q[3];
+                const uint32_t mv0[5] = {a0.x, a0.y, a0.z, a0.w, a4.x};
+                const uint32_t mv1[5] = {a1.x, a1.y, a1.z, a1.w, a4.y};
+                cmp_word(base0, slab0, r, s0, xs[e], h.x, mv0, (int)h.z);
+                cmp_word(base1, slab1, r, s1, xs[e], h.y, mv1, (int)h.w);
             }
         }
     }
     // the bias sample, then zeros up to the set's K-steps (8 words each)
-    cmp_push(base0, r, st0, 1u, 1);
-    for (const int words = 8 * ks0; st0.word < words;) {
-        cmp_emit(base0, r, st0, (uint32_t)st0.acc);
-        st0.acc >>= 32;
+    cmp_push(base0, slab0, r, s0, 1u, 1);
+    cmp_push(base1, slab1, r, s1, 1u, 1);
+    for (const int words = 8 * ks0; s0.word < words;) {
+        cmp_emit(base0, slab0, r, s0, (uint32_t)s0.acc);
+        s0.acc >>= 32;
     }
-    cmp_push(base1, r, st1, 1u, 1);
-    for (const int words = 8 * ks1; st1.word < words;) {
-        cmp_emit(base1, r, st1, (uint32_t)st1.acc);
-        st1.acc >>= 32;
+    for (const int words = 8 * ks1; s1.word < words;) {
+        cmp_emit(base1, slab1, r, s1, (uint32_t)s1.acc);
+        s1.acc >>= 32;
     }
 }
 
@@ -617,7 +655,7 @@ cudaError_t launch_compact(const Planes& pl, const CmpFirst* firsts, int i0, int
                            uint8_t* cmp, cudaStream_t st) {
     if (n_first == 0) return cudaSuccess;
     const dim3 grid((pl.M + 63) / 64, n_first, 2);
-    compact_kernel<<<grid, 128, 0, st>>>(pl, firsts, i0, cmp);
+    compact_kernel<<<grid, kCompactThreads, 0, st>>>(pl, firsts, i0, cmp);
     return cudaGetLastError();
 }
 
