@@ -216,8 +216,10 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
  * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with
  * epi3_get_stats); "profile" = "0" | "1" (per-role wait accounting inside the tensor-core
  * scan kernel, reported in epi3_stats); "mma_form" = "auto" | "plain" | "split" (the
- * tensor-core scan kernel's form: 14 warps with 128 registers each, or 16 warps that move
- * registers to the epilogue; "auto" lets the tuner time both for the shape).  Unknown keys or values: EPI3_ERR_ARG, or EPI3_ERR_UNSUPPORTED
+ * tensor-core scan kernel's form: for EPI3_PATH_MMA4 (and mma, mma16) 14 warps with 128
+ * registers each, or 16 warps that move registers to the epilogue; for EPI3_PATH_MMA4C an
+ * epilogue that takes a lane's triplets one at a time, or both together in f32x2 instructions;
+ * "auto" lets the tuner time both for the shape).  Unknown keys or values: EPI3_ERR_ARG, or EPI3_ERR_UNSUPPORTED
  * for a path that is not available.  "cmp_buffer_mb" = device memory (MiB, default 2048) for
  * the compacted chunks of EPI3_PATH_MMA4C: the first SNPs are compacted and scanned in ranges
  * whose chunks fit it (a range needs at least one first SNP's chunks).
@@ -254,6 +256,10 @@ typedef struct {
     /* sample-compacted form (EPI3_PATH_MMA4C): device time of the compaction kernels, a part
        of scan_kernel_ms (0 for the other forms) */
     float compact_ms;
+    /* form of the tensor scan that ran: 1 = plain (one-hot: 14 warps of 128 registers;
+       compacted: one triplet per lane at a time), 2 = split / paired (one-hot: registers moved
+       to the epilogue; compacted: a lane's two triplets in f32x2 instructions); 0 = POPC */
+    int32_t form;
 } epi3_stats;
 
 int epi3_get_stats(const epi3_handle* h, epi3_stats* out);

@@ -536,6 +536,11 @@ bool mma_split(const epi3_handle* h, int kind) {
     (void)kind;
     return h->mma_form == 0 ? h->tuned_form == 2 : h->mma_form == 2;
 }
+// Paired epilogue of the compacted form (option "mma_form" = split, or the tuner's choice).
+bool cmp_paired(const epi3_handle* h) {
+    return h->mma_form == 0 ? (h->tuned_form_path == EPI3_PATH_MMA4C && h->tuned_form == 2)
+                            : h->mma_form == 2;
+}
 
 CohortDev cohort_of(const epi3_handle* h, long long pb, long long pe, int top_k) {
     CohortDev cd{};
@@ -611,6 +616,7 @@ int scan_mma_impl(epi3_handle* h, int path, long long pb, long long pe, long lon
     s.path = path;
     s.grid = grid;
     s.block = mma_threads(mma_split(h, kind_of_path(path)));
+    s.form = mma_split(h, kind_of_path(path)) ? 2 : 1;
     s.kernel_launches = 5;
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
     s.wait_producers_tmem = s.mma_issue = 0.f;
@@ -782,7 +788,7 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
             a.n_tiles = range_tiles[r];
             a.cmp = h->d_cmp;
             a.prof = h->profile ? h->d_prof : nullptr;
-            CK(launch_scan_cmp(a, grid, h->stream, h->tsum != nullptr || h->profile),
+            CK(launch_scan_cmp(a, grid, h->stream, h->tsum != nullptr || h->profile, cmp_paired(h)),
                "compacted scan launch");
         }
         CK(cudaEventRecord(h->ev[2], h->stream), "event");
@@ -805,6 +811,7 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
     s.path = EPI3_PATH_MMA4C;
     s.grid = grid;
     s.block = 512;
+    s.form = cmp_paired(h) ? 2 : 1;
     s.kernel_launches = 2 * n_ranges + 3;
     s.wait_loader = s.wait_mma_operands = s.wait_mma_accum = s.wait_producers = s.wait_epilogue = 0.f;
     s.wait_producers_tmem = s.mma_issue = 0.f;
@@ -850,7 +857,8 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     // measure the path (auto) or the tensor-scan form (form auto) once per shape bucket
     if (!h->tuning && h->autotune &&
         ((h->path == EPI3_PATH_AUTO && !h->tuned_path) ||
-         (is_mma_path(resolve_path(h)) && h->mma_form == 0 && h->tuned_form_path != resolve_path(h)))) {
+         ((is_mma_path(resolve_path(h)) || resolve_path(h) == EPI3_PATH_MMA4C) && h->mma_form == 0 &&
+          h->tuned_form_path != resolve_path(h)))) {
         const int rc = tune_handle(h);
         if (rc != EPI3_OK) return rc;
     }
@@ -965,6 +973,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
     s.k2_rel_bound = h->k2.rel;
     s.k2_abs_bound = h->k2.abs_;
     s.k2_prune_bound = h->k2.prune_delta;
+    s.form = 0;
     s.compact_ms = 0.f;
     cudaEventElapsedTime(&s.scan_kernel_ms, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&s.select_ms, h->ev[2], h->ev[3]);
@@ -1492,7 +1501,8 @@ int tune_handle(epi3_handle* h) {
     std::vector<Choice> cands;
     if (want_path) {
         cands.push_back({EPI3_PATH_POPC8, 0});
-        cands.push_back({EPI3_PATH_MMA4C, 0});
+        cands.push_back({EPI3_PATH_MMA4C, 1});
+        cands.push_back({EPI3_PATH_MMA4C, 2});
         if (mma_tile_estimate(h->M) <= kMaxMmaTiles) {
             cands.push_back({EPI3_PATH_MMA4, 1});
             cands.push_back({EPI3_PATH_MMA4, 2});
@@ -1509,10 +1519,8 @@ int tune_handle(epi3_handle* h) {
         if (e.dev == dev && e.sms == h->sm_count && e.mb == mb && e.nb == nb && e.scope == scope &&
             (scope == 1 || e.path == fixed)) {
             if (want_path) h->tuned_path = e.path;
-            if (e.form) {
-                h->tuned_form = e.form;
-                h->tuned_form_path = e.path;
-            }
+            h->tuned_form = e.form ? e.form : 1;
+            h->tuned_form_path = e.path;
             return EPI3_OK;
         }
     const long long np = pairs(h->M - 1);
@@ -1566,10 +1574,8 @@ int tune_handle(epi3_handle* h) {
     if (best < 0) return fail(EPI3_ERR_UNSUPPORTED, "no scan form serves %d SNPs", h->M);
     const Choice c = cands[(size_t)best];
     if (want_path) h->tuned_path = c.path;
-    if (c.form) {
-        h->tuned_form = c.form;
-        h->tuned_form_path = c.path;
-    }
+    h->tuned_form = c.form ? c.form : 1;
+    h->tuned_form_path = c.path;
     TuneEntry e;
     e.dev = dev;
     e.sms = h->sm_count;

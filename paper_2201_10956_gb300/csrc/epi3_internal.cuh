@@ -209,7 +209,8 @@ size_t scan_cmp_smem();
 // compaction of first SNPs i0 .. i0 + n_first - 1 into cmp (chunk indices from firsts)
 cudaError_t launch_compact(const Planes& pl, const CmpFirst* firsts, int i0, int n_first,
                            uint8_t* cmp, cudaStream_t st);
-cudaError_t launch_scan_cmp(const CmpArgs& a, int grid, cudaStream_t st, bool checksum);
+// instrumented: table checksums / wait profile; paired: the two-triplets-per-lane epilogue
+cudaError_t launch_scan_cmp(const CmpArgs& a, int grid, cudaStream_t st, bool instrumented, bool paired);
 
 // tiles[t] = (i, j-block, k-block, cohort); a CTA takes tiles blockIdx.x, +gridDim.x, ...
 // split: the register-split form of the kernel (measured per shape by the handle tuner, per

@@ -208,6 +208,7 @@ constexpr int kCmpRegions = 7;           // 64-column accumulator regions (colum
 constexpr uint32_t kCmpSfCol = 480;      // block scales: A at 480..495, B at 496..511
 constexpr int kCmpThreads = 512;
 constexpr int kCmpEpiWarp0 = 4, kCmpEpiWarps = 12, kCmpEpiThreads = kCmpEpiWarps * 32;
+constexpr int kCmpEpiParts = kCmpEpiWarps / 4;   // epilogue warps per tensor-memory lane quadrant
 constexpr int kCmpRegLaunch = 128, kCmpRegCtl = 56, kCmpRegEpi = 152;
 static_assert(kCmpRegCtl + 3 * kCmpRegEpi == 4 * kCmpRegLaunch, "register split");
 static_assert(kCmpThreads * kCmpRegLaunch == 65536, "the launch holds the whole register file");
@@ -272,8 +273,11 @@ __device__ __forceinline__ CmpTile cmp_tile(const CmpArgs& a, long long t) {
 // kInstr: the instrumented instantiation (table checksums; with a.prof, per role the cycles spent
 // waiting, summed over CTAs: [0] loader on free slots, [1] MMA issuer on loaded slots, [2] MMA
 // issuer on free accumulator regions, [4] epilogue thread 0 on finished tiles, [5] kernel cycles,
-// [7] MMA issuer issuing MMAs and commits)
-template <bool kInstr>
+// [7] MMA issuer issuing MMAs and commits).
+// kPaired: the epilogue derives the cells and the bound of a lane's two triplets together in
+// f32x2 instructions (fewer instructions, more registers live: faster where the MMA pipeline
+// bounds the scan, slower where the epilogue does; the tuner measures both).
+template <bool kInstr, bool kPaired>
 __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs a) {
     const long long t_start = kInstr ? clock64() : 0;
     unsigned long long* const prof = kInstr ? a.prof : nullptr;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
             mx[1] = __ldg(pt.marg + M + i);
             const RowCells rcl[2] = {row_cells(pxy[0], mx[0], my[0], pt.n_c[0]),
                                      row_cells(pxy[1], mx[1], my[1], pt.n_c[1])};
-            for (int unit = part; unit < kTK / 4; unit += 3) {
+            for (int unit = part; unit < kTK / 4; unit += kCmpEpiParts) {
                 const float thr_g = __uint_as_float(*(volatile unsigned*)&ctrl->thr);
                 // this lane's two triplets: k = kb0 + 4 unit + 2 bme + m; pair-table rows first
                 float4 tik[2][2], tjk[2][2];
@@ -558,12 +562,11 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         rcv[q][e] = __shfl_xor_sync(0xffffffffu, bme ? v[q][e] : v[q][4 + e], 1);
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int k = kb0 + 4 * unit + 2 * bme + m;
-                    if (!(jrow && k > j && k < M)) continue;
-                    // n8[c][4 a + 2 b + z] = count + 1
-                    float n8[2][8];
+                // paired form: both triplets of the lane at once (lane x of every float2 is
+                // m = 0, lane y m = 1): the derived cells and the bound in f32x2 instructions
+                float2 u0p[kCells], u1p[kCells], bnd = make_float2(0.f, 0.f);
+                if constexpr (kPaired) {
+                    float2 n8p[2][8];  // n8p[c][4 a + 2 b + z] = count + 1
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -573,17 +576,56 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
 #pragma unroll
                                 for (int z = 0; z < 2; ++z) {
                                     const int q = 2 * c + aa;
-                                    const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
-                                    const uint32_t oth = rcv[q][2 * m + z];
-                                    n8[c][4 * aa + 2 * bb + z] = __uint_as_float(bb == bme ? own : oth);
+                                    float e[2];
+#pragma unroll
+                                    for (int m = 0; m < 2; ++m) {
+                                        const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
+                                        const uint32_t oth = rcv[q][2 * m + z];
+                                        e[m] = __uint_as_float(bb == bme ? own : oth);
+                                    }
+                                    n8p[c][4 * aa + 2 * bb + z] = make_float2(e[0], e[1]);
                                 }
-                    float u0[kCells], u1[kCells];
-                    cells_u(n8[0], rcl[0], tik[m][0], tjk[m][0], tmk[m][0], u0);
-                    cells_u(n8[1], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
+                    cells_u2(n8p[0], rcl[0], tik[0][0], tik[1][0], tjk[0][0], tjk[1][0], tmk[0][0],
+                             tmk[1][0], u0p);
+                    cells_u2(n8p[1], rcl[1], tik[0][1], tik[1][1], tjk[0][1], tjk[1][1], tmk[0][1],
+                             tmk[1][1], u1p);
+                    if (pruning) bnd = k2_bound_pair(u0p, u1p);
+                }
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int k = kb0 + 4 * unit + 2 * bme + m;
+                    if (!(jrow && k > j && k < M)) continue;
                     // most tables lie far above the band: prove it from the table-free
                     // approximation and skip the exact score's log-table gathers
-                    if (pruning && __fsub_rn(k2_bound_u(u0, u1), prune) > fminf(es.tloc, thr_g))
-                        continue;
+                    float u0[kCells], u1[kCells];
+                    if constexpr (kPaired) {
+                        if (pruning && __fsub_rn(m ? bnd.y : bnd.x, prune) > fminf(es.tloc, thr_g))
+                            continue;
+#pragma unroll
+                        for (int q = 0; q < kCells; ++q) {
+                            u0[q] = m ? u0p[q].y : u0p[q].x;
+                            u1[q] = m ? u1p[q].y : u1p[q].x;
+                        }
+                    } else {
+                        float n8[2][8];  // n8[c][4 a + 2 b + z] = count + 1
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+#pragma unroll
+                            for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+                                for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                                    for (int z = 0; z < 2; ++z) {
+                                        const int q = 2 * c + aa;
+                                        const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
+                                        const uint32_t oth = rcv[q][2 * m + z];
+                                        n8[c][4 * aa + 2 * bb + z] = __uint_as_float(bb == bme ? own : oth);
+                                    }
+                        cells_u(n8[0], rcl[0], tik[m][0], tjk[m][0], tmk[m][0], u0);
+                        cells_u(n8[1], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
+                        if (pruning && __fsub_rn(k2_bound_u(u0, u1), prune) > fminf(es.tloc, thr_g))
+                            continue;
+                    }
                     int r0[kCells], r1[kCells];
                     if (!counts_of(u0, u1, pt.n_c[0], pt.n_c[1], r0, r1)) {
                         atomicOr(&ctrl->status, kStBadCount);
@@ -659,7 +701,7 @@ cudaError_t launch_compact(const Planes& pl, const CmpFirst* firsts, int i0, int
     return cudaGetLastError();
 }
 
-template <bool kInstr>
+template <bool kInstr, bool kPaired>
 static cudaError_t launch_cmp_variant(const CmpArgs& a, int grid, cudaStream_t st) {
     const size_t smem = scan_cmp_smem();
     // once per device: the register split adds up to exactly the launch's registers, so refuse a
@@ -672,23 +714,27 @@ static cudaError_t launch_cmp_variant(const CmpArgs& a, int grid, cudaStream_t s
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(ready.load(std::memory_order_acquire) & bit)) {
         cudaFuncAttributes fa{};
-        e = cudaFuncGetAttributes(&fa, scan_cmp_kernel<kInstr>);
+        e = cudaFuncGetAttributes(&fa, scan_cmp_kernel<kInstr, kPaired>);
         if (e != cudaSuccess) return e;
         if (fa.numRegs != kCmpRegLaunch) return cudaErrorInvalidConfiguration;
-        e = cudaFuncSetAttribute(scan_cmp_kernel<kInstr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(scan_cmp_kernel<kInstr, kPaired>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         ready.fetch_or(bit, std::memory_order_release);
     }
     if (a.n_tiles == 0) return cudaSuccess;
-    scan_cmp_kernel<kInstr><<<grid, kCmpThreads, smem, st>>>(a);
+    scan_cmp_kernel<kInstr, kPaired><<<grid, kCmpThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 // The instrumented instantiation serves table checksums and wait profiles only, so the product
 // kernel carries no hook.
-cudaError_t launch_scan_cmp(const CmpArgs& a, int grid, cudaStream_t st, bool instrumented) {
-    return instrumented ? launch_cmp_variant<true>(a, grid, st) : launch_cmp_variant<false>(a, grid, st);
+cudaError_t launch_scan_cmp(const CmpArgs& a, int grid, cudaStream_t st, bool instrumented, bool paired) {
+    if (paired)
+        return instrumented ? launch_cmp_variant<true, true>(a, grid, st)
+                            : launch_cmp_variant<false, true>(a, grid, st);
+    return instrumented ? launch_cmp_variant<true, false>(a, grid, st)
+                        : launch_cmp_variant<false, false>(a, grid, st);
 }
 
 }  // namespace epi3

@@ -258,6 +258,95 @@ __device__ __forceinline__ void k2_bound_u2(const float* u0a, const float* u1a, 
                            -27.f * 0.9189385332046727f);
 }
 
+// Two FP32 lanes per 64-bit register (two tables at once): the f32x2 instructions of sm_100 and
+// later round each lane exactly like the scalar __fadd_rn / __fsub_rn / __fmaf_rn, so every lane
+// equals the scalar code's result bit for bit.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 x, y, r;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+        " add.rn.f32x2 r, x, y;\n mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 x, y, r;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+        " sub.rn.f32x2 r, x, y;\n mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 x, y, z, r;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+        " mov.b64 z, {%6, %7};\n fma.rn.f32x2 r, x, y, z;\n mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_dup(float a) { return make_float2(a, a); }
+
+// cells_u of two tables at once (lane x, lane y) sharing the row cells of one (i, j) pair and
+// class: the same operations in the same order as cells_u, two lanes per instruction.
+__device__ __forceinline__ void cells_u2(const float2* n8, const RowCells& rc, float4 pxz0,
+                                         float4 pxz1, float4 pyz0, float4 pyz1, float2 mz0,
+                                         float2 mz1, float2* u) {
+    const float2 xz[2][2] = {{make_float2(pxz0.x, pxz1.x), make_float2(pxz0.y, pxz1.y)},
+                             {make_float2(pxz0.z, pxz1.z), make_float2(pxz0.w, pxz1.w)}};
+    const float2 yz[2][2] = {{make_float2(pyz0.x, pyz1.x), make_float2(pyz0.y, pyz1.y)},
+                             {make_float2(pyz0.z, pyz1.z), make_float2(pyz0.w, pyz1.w)}};
+    const float2 z2[2] = {f2_sub(f2_sub(make_float2(mz0.x, mz1.x), xz[0][0]), xz[1][0]),
+                          f2_sub(f2_sub(make_float2(mz0.y, mz1.y), xz[0][1]), xz[1][1])};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float2 c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
+            u[9 * a + 3 * b] = c0;
+            u[9 * a + 3 * b + 1] = c1;
+            u[9 * a + 3 * b + 2] = f2_sub(f2_sub(f2_dup(rc.xy[2 * a + b]), c0), c1);
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+            u[9 * a + 6 + z] = f2_sub(f2_sub(xz[a][z], u[9 * a + z]), u[9 * a + 3 + z]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+            u[18 + 3 * b + z] = f2_sub(f2_sub(yz[b][z], u[3 * b + z]), u[9 + 3 * b + z]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+        u[9 * a + 8] = f2_sub(f2_sub(f2_dup(rc.xa2[a]), u[9 * a + 6]), u[9 * a + 7]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+        u[18 + 3 * b + 2] = f2_sub(f2_sub(f2_dup(rc.x2b[b]), u[18 + 3 * b]), u[18 + 3 * b + 1]);
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+        u[24 + z] = f2_sub(f2_sub(z2[z], u[18 + z]), u[21 + z]);
+    u[26] = f2_sub(f2_sub(f2_dup(rc.c22), u[24]), u[25]);
+}
+
+// k2_bound_u of two tables at once (lane x, lane y): the same chains in the same order.
+__device__ __forceinline__ float2 k2_bound_pair(const float2* u0, const float2* u1) {
+    float2 acc[2] = {f2_dup(0.f), f2_dup(0.f)};
+    const float2 half = f2_dup(0.5f);
+#pragma unroll
+    for (int q = 0; q < kCells; ++q) {
+        float2& a = acc[q < 14 ? 0 : 1];
+        const float2 us = f2_add(u0[q], u1[q]);
+        const float2 ls = make_float2(lg2_hw(us.x), lg2_hw(us.y));
+        const float2 l0 = make_float2(lg2_hw(u0[q].x), lg2_hw(u0[q].y));
+        const float2 l1 = make_float2(lg2_hw(u1[q].x), lg2_hw(u1[q].y));
+        a = f2_fma(f2_sub(us, half), ls, a);
+        // 1/2 - u: round-to-nearest is symmetric, so this is the scalar code's -(u - 1/2) exactly
+        a = f2_fma(f2_sub(half, u0[q]), l0, a);
+        a = f2_fma(f2_sub(half, u1[q]), l1, a);
+    }
+    const float2 s = f2_add(acc[0], acc[1]);
+    return make_float2(__fmaf_rn(0.6931471805599453f, s.x, -27.f * 0.9189385332046727f),
+                       __fmaf_rn(0.6931471805599453f, s.y, -27.f * 0.9189385332046727f));
+}
+
 // Exact integer cells r = u - 1 of both classes; false unless every cell lies in [0, N_c]
 // (which keeps every log-factorial lookup of the table in range).
 __device__ __forceinline__ bool counts_of(const float* u0, const float* u1, int n0, int n1,

@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
                 ("wait_mma_accum", ctypes.c_float), ("wait_producers", ctypes.c_float),
                 ("wait_epilogue", ctypes.c_float), ("wait_producers_tmem", ctypes.c_float),
                 ("mma_issue", ctypes.c_float), ("k2_prune_bound", ctypes.c_float),
-                ("compact_ms", ctypes.c_float)]
+                ("compact_ms", ctypes.c_float), ("form", ctypes.c_int32)]
 
 
 _lib = None

@@ -67,6 +67,7 @@ def test_checksum_equals_oracle_tables(m, n, n1):
         for form in ("plain", "split"):
             h.set_option("mma_form", form)
             assert h.scan_checksum(epi.PATH_MMA4) == want, form
+            assert h.scan_checksum(epi.PATH_MMA4C) == want, form
         # the handle still scans normally afterwards
         tr, sc = h.scan(5)
     otr, osc, _ = oracle.scan_topk(g, ph, 5)
@@ -126,10 +127,10 @@ def test_medium_workload_all_tables_equal_oracle():
     assert want[1] == 1024 * 1023 * 1022 // 6
     with epi.Handle(d.genotypes, d.phenotype) as h:
         assert h.scan_checksum(epi.PATH_POPC8) == want
-        assert h.scan_checksum(epi.PATH_MMA4C) == want
         for form in ("plain", "split"):
             h.set_option("mma_form", form)
             assert h.scan_checksum(epi.PATH_MMA4) == want, form
+            assert h.scan_checksum(epi.PATH_MMA4C) == want, form
 
 
 @pytest.mark.parametrize("config", ["medium", "large", "stress"])
@@ -145,6 +146,10 @@ def test_full_size_tables_agree(config):
             assert h.scan_checksum(PATHS[name]) == ref, name
         h.set_option("mma_form", "split" if config == "large" else "plain")  # the other form
         assert h.scan_checksum(epi.PATH_MMA4) == ref
+        h.set_option("mma_form", "split")
+        assert h.scan_checksum(epi.PATH_MMA4C) == ref
+        h.set_option("mma_form", "plain")
+        assert h.scan_checksum(epi.PATH_MMA4C) == ref
 
 
 @pytest.mark.parametrize("name", ["popc8", "mma4", "mma4c"])

@@ -210,6 +210,15 @@ def test_both_kernel_forms(m, n, n1):
             tr, sc = h.scan(12)
             assert h.stats()["block"] == threads
             assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
+        # the compacted form's two epilogues (one triplet per lane at a time, or a lane's two
+        # triplets in f32x2 instructions)
+        h.set_option("path", "mma4c")
+        for form, want in (("plain", 1), ("split", 2)):
+            h.set_option("mma_form", form)
+            check_every_triplet(h, g, ph, epi.PATH_MMA4C)
+            tr, sc = h.scan(12)
+            assert h.stats()["form"] == want
+            assert np.array_equal(tr, otr) and np.array_equal(sc, osc)
         with pytest.raises(epi.Epi3Error) as ei:
             h.set_option("mma_form", "wide")
         assert ei.value.code == epi.ERR_ARG

@@ -51,20 +51,20 @@ def test_autotune_off_takes_the_compacted_form():
         _oracle_equal(g, ph, tr, sc, 6)
 
 
-def test_explicit_tensor_path_tunes_only_its_form():
+@pytest.mark.parametrize("name,code", [("mma4", epi.PATH_MMA4), ("mma4c", epi.PATH_MMA4C)])
+def test_explicit_tensor_path_tunes_only_its_form(name, code):
     g, ph = pins.tiny_data(70, 2100, 1000, seed=33)
     with epi.Handle(g, ph) as h:
-        h.set_option("path", "mma4")
+        h.set_option("path", name)
         tr, sc = h.scan(5)
         st = h.stats()
-        assert st["path"] == epi.PATH_MMA4
-        blocks = set()
-        for form in ("plain", "split"):
-            h.set_option("mma_form", form)
-            h.scan(5)
-            blocks.add(h.stats()["block"])
-        assert st["block"] in blocks and len(blocks) == 2
+        assert st["path"] == code and st["form"] in (1, 2)
         _oracle_equal(g, ph, tr, sc, 5)
+        for form, want in (("plain", 1), ("split", 2)):
+            h.set_option("mma_form", form)
+            tr2, sc2 = h.scan(5)
+            assert h.stats()["form"] == want
+            assert np.array_equal(tr2, tr) and np.array_equal(sc2, sc)
 
 
 _CHILD = r'''
@@ -77,7 +77,7 @@ g, ph = pins.tiny_data(200, 3100, 1400, seed=34)
 with epi.Handle(g, ph) as h:
     tr, sc = h.scan(6)
     np.save({out!r}, np.concatenate([tr.astype(np.float64).ravel(), sc]))
-    print(h.stats()["path"], h.stats()["block"])
+    print(h.stats()["path"], h.stats()["form"])
 '''
 
 
@@ -87,8 +87,8 @@ def _child(cache, out):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
-    path, block = (int(x) for x in r.stdout.split()[-2:])
-    return path, block, np.load(out)
+    path, form = (int(x) for x in r.stdout.split()[-2:])
+    return path, form, np.load(out)
 
 
 def test_tune_cache_forces_each_choice(tmp_path):
@@ -102,18 +102,14 @@ def test_tune_cache_forces_each_choice(tmp_path):
     otr, osc, _ = oracle.scan_topk(g, ph, 6)
     ref = np.concatenate([otr.astype(np.float64).ravel(), osc])
     assert np.array_equal(res0, ref)
-    blocks = {}
-    for path, form in ((epi.PATH_POPC8, 0), (epi.PATH_MMA4C, 0), (epi.PATH_MMA4, 1),
-                       (epi.PATH_MMA4, 2)):
+    for path, form in ((epi.PATH_POPC8, 0), (epi.PATH_MMA4C, 1), (epi.PATH_MMA4C, 2),
+                       (epi.PATH_MMA4, 1), (epi.PATH_MMA4, 2)):
         row = list(mine[-1])
         row[4], row[5] = str(path), str(form)
         cache.write_text("\t".join(row) + "\n")
-        got_path, block, res = _child(cache, out)
-        assert got_path == path
-        if path == epi.PATH_MMA4:
-            blocks[form] = block
+        got_path, got_form, res = _child(cache, out)
+        assert (got_path, got_form) == (path, form)
         assert np.array_equal(res, ref), (path, form)
-    assert blocks[1] != blocks[2]
 
 
 @pytest.mark.parametrize("form", [None, "plain", "split"])
