@@ -320,18 +320,25 @@ def run_batch(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(local_rank)
     peaks = read_peaks()
     kern_s = statistics.mean(kern_ms) / 1000.0
-    mma_units = sum(gen.n_triplets(d.n_snps) * d.n_samples for d, p in zip(cohorts, paths) if p == 5)
+    # tensor work: 16 FLOP per sample-triplet of the one-hot cohorts, 8 per sample-triplet with a
+    # first-SNP genotype in {0,1} of the compacted ones
+    flop = sum(gen.n_triplets(d.n_snps) * d.n_samples * 16.0 for d, p in zip(cohorts, paths) if p == 5)
+    flop += sum(gen.n_triplets(d.n_snps) * d.n_samples * 8.0 * compacted_fraction(d.genotypes)
+                for d, p in zip(cohorts, paths) if p == 6)
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    achieved = mma_units * 16.0 / kern_s / 1e12
-    roofline = {"bound": "tensor", "kernel": "scan_mma_kernel<e2m1> (one persistent launch, all "
-                "tensor-path cohorts) + scan_popc_kernel<8-cell> launches",
+    achieved = flop / kern_s / 1e12
+    roofline = {"bound": "tensor", "kernel": "scan_mma_kernel<e2m1> (one persistent launch, the "
+                "one-hot cohorts) + scan_cmp_kernel launches (compacted cohorts) + "
+                "scan_popc_kernel<8-cell> launches",
                 "achieved": achieved, "peak": 6 * bf16, "unit": "TFLOP/s",
                 "frac": achieved / (6 * bf16), "traffic": None,
                 "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst) x 6 (e2m1/bf16 "
                              "nominal ratio)",
-                "work_note": "16 FLOP per sample-triplet of the tensor-path cohorts over the "
-                             "whole scan phase (POPC cohorts' time included)",
+                "work_note": "16 FLOP per sample-triplet of the one-hot cohorts, 8 per "
+                             "compacted sample-triplet of the compacted cohorts, over the whole "
+                             "scan phase (POPC cohorts' time included)",
                 "kernel_ms": 1000 * kern_s, "tensor_cohorts": int((paths == 5).sum()),
+                "compacted_cohorts": int((paths == 6).sum()),
                 "popc8_cohorts": int((paths == 2).sum())}
     e2e = None
     if not args.no_e2e and world == 1:

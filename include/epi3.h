@@ -210,7 +210,7 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
  * if set, for later processes) | "popc" | "popc8" | "mma" | "mma16" | "mma4" | "mma4c";
  * "autotune" = "1" (default) | "0" (no measuring: auto = EPI3_PATH_MMA4C, form plain);
  * "candidates" = initial length of the FP32 candidate list (64 .. 2^28; default 2^20 from
- * 2^26 triplets on, else 2^16; a scan that overflows it grows it 8x and runs again);
+ * 2^22 triplets on, else 2^16; a scan that overflows it grows it 8x and runs again);
  * "threads" = threads per block of the POPC scan kernels (64..256, multiple of 32);
  * "ctas_per_sm" = persistent CTAs per SM of the POPC scans (0 = occupancy maximum);
  * "timing" = "0" | "1" (record CUDA events around the scan's kernels, read back with
@@ -302,11 +302,12 @@ int epi3_scan_noalloc(const uint8_t* genotypes, const uint8_t* phenotype, int32_
 
 /*
  * Batches: many independent data sets ("cohorts") of uneven size scanned together.  Each
- * cohort is packed like epi3_create; a tuner times the tensor-core and 8-cell POPC scan
- * kernels on each cohort's heaviest pair slice and keeps the faster (per M/64, N/1024
- * bucket; persisted in the file named by EPI3_TUNE_CACHE; EPI3_BATCH_PATH=mma|popc8
- * forces one, "mma" being the E2M1 tensor-core form of EPI3_PATH_MMA4).  The tensor-core cohorts share ONE persistent tcgen05 launch over all their
- * tiles; the whole scan + candidate stages + read-back is captured once in a CUDA graph and
+ * cohort is packed like epi3_create; a cohort too small to fill the GPU alone joins the
+ * shared one-hot tensor launch, every other one gets the handle tuner's measured choice for its
+ * shape (8-cell POPC, the compacted tensor form in launches of its own, or the shared one-hot
+ * launch; per M/64, N/1024 bucket; persisted in the file named by EPI3_TUNE_CACHE;
+ * EPI3_BATCH_PATH = mma | mma4c | popc8 forces one).  The one-hot tensor cohorts share ONE
+ * persistent tcgen05 launch over all their tiles; the whole scan + candidate stages + read-back is captured once in a CUDA graph and
  * replayed by every epi3_batch_scan.  The answer of each cohort is the one epi3_scan gives.
  *
  *   cohorts[c]    {genotypes, phenotype, n_snps, n_samples} as epi3_create.
@@ -330,10 +331,14 @@ int epi3_batch_destroy(epi3_batch* b);
 /* Figures of the last epi3_batch_scan: scan_kernel_ms = total_ms = device time of the graph
  * replay; pack_ms holds the tuner's time at create. */
 int epi3_batch_get_stats(const epi3_batch* b, epi3_stats* out);
-/* The path (EPI3_PATH_MMA4 or EPI3_PATH_POPC8) the tuner chose for each cohort. */
+/* The path the tuner chose for each cohort: EPI3_PATH_MMA4 (the shared one-hot tensor launch),
+ * EPI3_PATH_MMA4C (compaction + compacted scan launches of its own in the graph) or
+ * EPI3_PATH_POPC8.  The environment variable EPI3_BATCH_PATH = "mma" | "mma4c" | "popc8" forces
+ * one for every cohort. */
 int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths);
-/* The tensor-scan form of each cohort: 0 = not a tensor cohort, 1 = plain, 2 = register-split,
- * -1 = not measured yet.  All tensor cohorts share one persistent launch and so one form,
+/* The tensor-scan form of each cohort: 0 = not a tensor cohort, 1 = plain, 2 = register-split
+ * (one-hot) or paired (compacted), -1 = not measured yet.  Compacted cohorts take the handle
+ * tuner's form for their shape.  All one-hot cohorts share one persistent launch and so one form,
  * measured on the first epi3_batch_scan by replaying the batch in both forms (the environment
  * variable EPI3_BATCH_FORM = "plain" | "split" forces one).  The tile (128 rows (j, b) x 256
  * columns (k, z) of the one-hot operands) is the kernel's only one: the tensor-memory budget

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <chrono>
 #include <vector>
 
 #include "epi3_internal.cuh"
@@ -310,9 +311,10 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     if (rc != EPI3_OK) return rc;
     if ((rc = build_k2_tables(h)) != EPI3_OK) return rc;
     // FP32 candidate list: the CTAs flush their in-band candidates before the shared threshold
-    // tightens, about 10^5 of them on a large scan (a list that overflows costs a whole rescan)
+    // tightens, about 10^5 of them on a scan that fills the GPU (a list that overflows costs a
+    // whole rescan, in a batch a second replay of every cohort)
     const long long m = h->M;
-    h->cand_cap = inject("cand") ? 128 : m * (m - 1) * (m - 2) / 6 >= (1LL << 26) ? 1LL << 20 : 1LL << 16;
+    h->cand_cap = inject("cand") ? 128 : m * (m - 1) * (m - 2) / 6 >= (1LL << 22) ? 1LL << 20 : 1LL << 16;
     CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "alloc candidates");
     CK(dev_alloc((void**)&h->d_fin, sizeof(Final) * kFinalCap), "alloc final");
     CK(dev_alloc((void**)&h->d_out_scores, sizeof(double) * EPI3_MAX_TOPK), "alloc out scores");
@@ -722,16 +724,31 @@ void plan_cmp(const epi3_handle* h, long long pb, long long pe, CmpPlan& P) {
     }
 }
 
-int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int top_k,
-                  int32_t* out_trip, double* out_scores, int32_t* n_out) {
+// The compaction plan of [pb, pe) for this handle, with its first-SNP table uploaded to
+// h->d_firsts (the marginals come to the host once per handle).
+int cmp_prepare(epi3_handle* h, long long pb, long long pe, CmpPlan& P) {
     const int M = h->M;
     if (h->h_marg.empty()) {
         h->h_marg.resize(2 * (size_t)M);
         CK(cudaMemcpy(h->h_marg.data(), h->d_marg, sizeof(int2) * 2 * (size_t)M,
                       cudaMemcpyDeviceToHost), "read marginals");
     }
-    CmpPlan P;
     plan_cmp(h, pb, pe, P);
+    cudaFree(h->d_firsts);
+    h->d_firsts = nullptr;
+    if (!P.firsts.empty()) {
+        CK(dev_alloc((void**)&h->d_firsts, sizeof(CmpFirst) * P.firsts.size()), "alloc first-SNP table");
+        CK(cudaMemcpyAsync(h->d_firsts, P.firsts.data(), sizeof(CmpFirst) * P.firsts.size(),
+                           cudaMemcpyHostToDevice, h->stream), "upload first-SNP table");
+    }
+    return EPI3_OK;
+}
+
+int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int top_k,
+                  int32_t* out_trip, double* out_scores, int32_t* n_out) {
+    CmpPlan P;
+    const int prc = cmp_prepare(h, pb, pe, P);
+    if (prc != EPI3_OK) return prc;
     const std::vector<CmpFirst>& firsts = P.firsts;
     const std::vector<int>& range_start = P.range_start;
     const std::vector<long long>& range_tiles = P.range_tiles;
@@ -745,13 +762,6 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
         h->cmp_bytes = 0;
         CK(dev_alloc((void**)&h->d_cmp, need), "alloc compacted chunks");
         h->cmp_bytes = need;
-    }
-    cudaFree(h->d_firsts);
-    h->d_firsts = nullptr;
-    if (!firsts.empty()) {
-        CK(dev_alloc((void**)&h->d_firsts, sizeof(CmpFirst) * firsts.size()), "alloc first-SNP table");
-        CK(cudaMemcpyAsync(h->d_firsts, firsts.data(), sizeof(CmpFirst) * firsts.size(),
-                           cudaMemcpyHostToDevice, h->stream), "upload first-SNP table");
     }
     const int grid = h->sm_count;
     const int n_ranges = (int)range_start.size();
@@ -1387,7 +1397,13 @@ struct epi3_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<epi3_handle*> h;
-    std::vector<int> path;              // EPI3_PATH_MMA4 or EPI3_PATH_POPC8 per cohort
+    std::vector<int> path;              // EPI3_PATH_MMA4, EPI3_PATH_MMA4C or EPI3_PATH_POPC8 per cohort
+    // compacted-form cohorts: per cohort its ranges of first SNPs (first SNP of each range,
+    // tiles of each range, end of the last), all compacting into one shared buffer
+    std::vector<std::vector<int>> cmp_start;
+    std::vector<std::vector<long long>> cmp_tiles;
+    std::vector<int> cmp_end;
+    uint8_t* d_cmp = nullptr;
     Ctrl* d_ctrls = nullptr;            // one control block per cohort, contiguous
     Ctrl* h_ctrls = nullptr;            // pinned
     CohortDev* d_cds = nullptr;
@@ -1421,6 +1437,7 @@ void batch_release(epi3_batch* b) {
     cudaFreeHost(b->h_ctrls);
     cudaFree(b->d_cds);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_cmp);
     cudaFree(b->d_scores);
     cudaFree(b->d_trip);
     cudaFreeHost(b->h_scores);
@@ -1592,40 +1609,21 @@ int tune_path(epi3_batch* b, epi3_handle* h, int* path_out, float* ms) {
     const char* force = getenv("EPI3_BATCH_PATH");
     if (force && !strcmp(force, "mma")) { *path_out = EPI3_PATH_MMA4; return EPI3_OK; }
     if (force && !strcmp(force, "popc8")) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
-    if (mma_tile_estimate(h->M) > kMaxMmaTiles) { *path_out = EPI3_PATH_POPC8; return EPI3_OK; }
-    // A cohort whose tensor tiles cannot fill the GPU on their own is latency-bound when timed
-    // alone, yet in the batch its tiles share one persistent launch with every other cohort's
-    // (its marginal cost there is its tiles' share of that launch, at the throughput-bound
-    // rate, several times the POPC forms').  Timing it alone would be biased toward POPC, so
-    // such cohorts take the tensor form; the rest are timed on a slice that does fill the GPU.
+    if (force && !strcmp(force, "mma4c")) { *path_out = EPI3_PATH_MMA4C; return EPI3_OK; }
+    // A cohort whose one-hot tensor tiles cannot fill the GPU on their own is latency-bound when
+    // timed alone, yet in the batch its tiles share one persistent launch with every other
+    // cohort's (its marginal cost there is its tiles' share of that launch, at the
+    // throughput-bound rate, several times the POPC forms').  Timing it alone would be biased
+    // against the shared launch, so such cohorts take it; the rest get the handle tuner's
+    // measured choice for their shape (8-cell POPC, the compacted form in launches of its own,
+    // or the shared one-hot launch).
     if (mma_tile_estimate(h->M) < 64LL * b->sm_count) { *path_out = EPI3_PATH_MMA4; return EPI3_OK; }
-    tune_load();
-    const std::string dev = device_name(b->device);
-    const int mb = h->M / 64, nb = h->N / 1024;
-    for (const TuneEntry& e : g_tune)
-        if (e.dev == dev && e.sms == b->sm_count && e.mb == mb && e.nb == nb &&
-            e.scope == 0 && (e.path == EPI3_PATH_MMA4 || e.path == EPI3_PATH_POPC8)) {
-            *path_out = e.path;
-            return EPI3_OK;
-        }
-    const long long np = pairs(h->M - 1);
-    const long long pe = std::max(1LL, np / 16);
-    float t[2] = {0.f, 0.f};
-    const int paths[2] = {EPI3_PATH_POPC8, EPI3_PATH_MMA4};
-    int32_t trip[3];
-    double sc;
-    int32_t nout = 0;
-    for (int q = 0; q < 2; ++q) {
-        h->path = paths[q];
-        int rc = scan_impl(h, 0, pe, 1, trip, &sc, &nout, false);  // set-up + warm-up
-        if (rc == EPI3_OK) rc = scan_impl(h, 0, pe, 1, trip, &sc, &nout, false);
-        if (rc != EPI3_OK) return rc;
-        t[q] = h->stats.scan_kernel_ms;
-        *ms += h->stats.total_ms * 2;
-    }
+    const auto t0 = std::chrono::steady_clock::now();
     h->path = EPI3_PATH_AUTO;
-    *path_out = t[1] <= t[0] ? EPI3_PATH_MMA4 : EPI3_PATH_POPC8;
-    tune_store(TuneEntry{dev, b->sm_count, mb, nb, *path_out});
+    const int rc = tune_handle(h);
+    if (rc != EPI3_OK) return rc;
+    *path_out = h->tuned_path;
+    *ms += std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return EPI3_OK;
 }
 
@@ -1654,6 +1652,12 @@ int batch_capture(epi3_batch* b, int top_k) {
         if (occ < 1) return fail(EPI3_ERR_UNSUPPORTED, "cohort %d does not fit the POPC scan", c);
         grid[c] = b->sm_count * occ;
     }
+    for (int c = 0; c < b->n; ++c)  // the compacted scan's function attributes, outside the capture
+        if (b->path[c] == EPI3_PATH_MMA4C) {
+            CmpArgs none{};
+            CK(launch_scan_cmp(none, b->sm_count, b->stream, false, cmp_paired(b->h[c])),
+               "compacted scan set-up");
+        }
     CK(cudaStreamSynchronize(b->stream), "descriptors");
 
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed), "begin capture");
@@ -1712,6 +1716,27 @@ int batch_capture(epi3_batch* b, int top_k) {
             static thread_local std::string detail;
             detail = buf;
             where = detail.c_str();
+        }
+    }
+    cur = "compacted scan";
+    for (int c = 0; c < b->n; ++c) {
+        if (b->path[c] != EPI3_PATH_MMA4C) continue;
+        cur_c = c;
+        epi3_handle* h = b->h[c];
+        const std::vector<int>& rs = b->cmp_start[c];
+        for (size_t r = 0; r < rs.size(); ++r) {
+            const int i0 = rs[r];
+            const int n = (r + 1 < rs.size() ? rs[r + 1] : b->cmp_end[c]) - i0;
+            ok(launch_compact(h->pl, h->d_firsts + i0, i0, n, b->d_cmp, b->stream));
+            CmpArgs a{};
+            a.cd = cds[c];
+            a.firsts = h->d_firsts + i0;
+            a.i0 = i0;
+            a.n_first = n;
+            a.n_tiles = b->cmp_tiles[c][r];
+            a.cmp = b->d_cmp;
+            a.prof = nullptr;
+            ok(launch_scan_cmp(a, b->sm_count, b->stream, false, cmp_paired(h)));
         }
     }
     cur = "candidate stage";
@@ -1815,15 +1840,30 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
         if ((rc = ensure_pair_tables(h)) != EPI3_OK) return bail(rc);
     }
     std::vector<int4> tiles;
+    size_t cmp_need = 0;
+    b->cmp_start.assign(n_cohorts, std::vector<int>());
+    b->cmp_tiles.assign(n_cohorts, std::vector<long long>());
+    b->cmp_end.assign(n_cohorts, 0);
     for (int c = 0; c < n_cohorts; ++c) {
         epi3_handle* h = b->h[c];
         if ((rc = tune_path(b, h, &b->path[c], &b->tune_ms)) != EPI3_OK) return bail(rc);
         if (b->path[c] == EPI3_PATH_MMA4) {
             if ((rc = ensure_onehot(h, kKindE2M1)) != EPI3_OK) return bail(rc);
             append_tiles(h->M, 0, pairs(h->M - 1), c, tiles);
+        } else if (b->path[c] == EPI3_PATH_MMA4C) {
+            // its own compaction + scan launches in the graph, ranges planned now
+            CmpPlan P;
+            if ((rc = ensure_pair_floats(h)) != EPI3_OK) return bail(rc);
+            if ((rc = cmp_prepare(h, 0, pairs(h->M - 1), P)) != EPI3_OK) return bail(rc);
+            b->cmp_start[c] = P.range_start;
+            b->cmp_tiles[c] = P.range_tiles;
+            b->cmp_end[c] = P.i_hi;
+            cmp_need = std::max(cmp_need, P.need);
         }
         h->path = b->path[c];
     }
+    if (cmp_need && (e = dev_alloc((void**)&b->d_cmp, cmp_need)) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc compacted chunks"));
     b->n_tiles = (long long)tiles.size();
     // the tensor launch's form (plain or register-split) is measured on the first scan, unless
     // EPI3_BATCH_FORM forces one
@@ -1984,7 +2024,8 @@ int epi3_batch_get_paths(const epi3_batch* b, int32_t* out_paths) {
 int epi3_batch_get_forms(const epi3_batch* b, int32_t* out_forms) {
     if (!b || !out_forms) return fail(EPI3_ERR_ARG, "null argument");
     for (int c = 0; c < b->n; ++c)
-        out_forms[c] = b->path[c] != EPI3_PATH_MMA4 ? 0 : !b->form_set ? -1 : b->split ? 2 : 1;
+        out_forms[c] = b->path[c] == EPI3_PATH_MMA4C ? (cmp_paired(b->h[c]) ? 2 : 1)
+                       : b->path[c] != EPI3_PATH_MMA4 ? 0 : !b->form_set ? -1 : b->split ? 2 : 1;
     return EPI3_OK;
 }
 

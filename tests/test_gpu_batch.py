@@ -32,7 +32,7 @@ def small_cohorts(seed=3):
     return out
 
 
-@pytest.mark.parametrize("force", [None, "mma", "popc8"])
+@pytest.mark.parametrize("force", [None, "mma", "mma4c", "popc8"])
 def test_batch_matches_oracle(monkeypatch, force):
     if force:
         monkeypatch.setenv("EPI3_BATCH_PATH", force)
@@ -41,7 +41,7 @@ def test_batch_matches_oracle(monkeypatch, force):
     with epi.Batch(data) as b:
         paths = b.paths()
         if force:
-            want = epi.PATH_MMA4 if force == "mma" else epi.PATH_POPC8
+            want = {"mma": epi.PATH_MMA4, "mma4c": epi.PATH_MMA4C, "popc8": epi.PATH_POPC8}[force]
             assert np.all(paths == want)
         for rep in range(2):  # the second scan replays the captured graph
             tr, sc = b.scan(k)
@@ -86,7 +86,7 @@ def test_batch_config_48_cohorts():
     with epi.Batch(data) as b:
         tr, sc = b.scan(5)
         paths = b.paths()
-    assert set(paths.tolist()) <= {epi.PATH_MMA4, epi.PATH_POPC8}
+    assert set(paths.tolist()) <= {epi.PATH_MMA4, epi.PATH_MMA4C, epi.PATH_POPC8}
     for c, d in enumerate(cohorts):
         g, ph = d.genotypes, d.phenotype
         assert np.array_equal(oracle.scores(g, ph, tr[c]), sc[c])
