@@ -563,10 +563,10 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                     for (int e = 0; e < 4; ++e)
                         rcv[q][e] = __shfl_xor_sync(0xffffffffu, bme ? v[q][e] : v[q][4 + e], 1);
                 // paired form: both triplets of the lane at once (lane x of every float2 is
-                // m = 0, lane y m = 1): the derived cells and the bound in f32x2 instructions
-                float2 u0p[kCells], u1p[kCells], bnd = make_float2(0.f, 0.f);
+                // m = 0, lane y m = 1): class 0's cells kept, class 1's derived on the fly into
+                // the bound (f32x2 instructions); survivors derive their class-1 cells again
+                float2 u0p[kCells], n8p[2][8], bnd = make_float2(0.f, 0.f);
                 if constexpr (kPaired) {
-                    float2 n8p[2][8];  // n8p[c][4 a + 2 b + z] = count + 1
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -587,9 +587,9 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                                 }
                     cells_u2(n8p[0], rcl[0], tik[0][0], tik[1][0], tjk[0][0], tjk[1][0], tmk[0][0],
                              tmk[1][0], u0p);
-                    cells_u2(n8p[1], rcl[1], tik[0][1], tik[1][1], tjk[0][1], tjk[1][1], tmk[0][1],
-                             tmk[1][1], u1p);
-                    if (pruning) bnd = k2_bound_pair(u0p, u1p);
+                    if (pruning)
+                        bnd = k2_bound_stream(u0p, n8p[1], rcl[1], tik[0][1], tik[1][1], tjk[0][1],
+                                              tjk[1][1], tmk[0][1], tmk[1][1]);
                 }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
@@ -602,10 +602,11 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                         if (pruning && __fsub_rn(m ? bnd.y : bnd.x, prune) > fminf(es.tloc, thr_g))
                             continue;
 #pragma unroll
-                        for (int q = 0; q < kCells; ++q) {
-                            u0[q] = m ? u0p[q].y : u0p[q].x;
-                            u1[q] = m ? u1p[q].y : u1p[q].x;
-                        }
+                        for (int q = 0; q < kCells; ++q) u0[q] = m ? u0p[q].y : u0p[q].x;
+                        float n81[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) n81[e] = m ? n8p[1][e].y : n8p[1][e].x;
+                        cells_u(n81, rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
                     } else {
                         float n8[2][8];  // n8[c][4 a + 2 b + z] = count + 1
 #pragma unroll

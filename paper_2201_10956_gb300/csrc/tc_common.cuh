@@ -326,22 +326,69 @@ __device__ __forceinline__ void cells_u2(const float2* n8, const RowCells& rc, f
     u[26] = f2_sub(f2_sub(f2_dup(rc.c22), u[24]), u[25]);
 }
 
-// k2_bound_u of two tables at once (lane x, lane y): the same chains in the same order.
-__device__ __forceinline__ float2 k2_bound_pair(const float2* u0, const float2* u1) {
+// k2_bound_u of two tables (lanes x, y) with class 1's cells derived on the fly (the same
+// operations as cells_u2) and each cell's three terms chained as soon as the cell is known, so
+// that class 1's 27 cells are never live at once.  The cells enter the two chains in another
+// order than in k2_bound_u;
+// the bound's error analysis (every finished cell adds a positive amount; 82 roundings of at
+// most 2^-24 of the largest partial sum) holds for any order.
+__device__ __forceinline__ float2 k2_bound_stream(const float2* u0, const float2* n8,
+                                                  const RowCells& rc, float4 pxz0, float4 pxz1,
+                                                  float4 pyz0, float4 pyz1, float2 mz0, float2 mz1) {
     float2 acc[2] = {f2_dup(0.f), f2_dup(0.f)};
     const float2 half = f2_dup(0.5f);
+    auto term = [&](int q, float2 u1) {
+        float2& a = acc[q & 1];
+        const float2 us = f2_add(u0[q], u1);
+        a = f2_fma(f2_sub(us, half), make_float2(lg2_hw(us.x), lg2_hw(us.y)), a);
+        a = f2_fma(f2_sub(half, u0[q]), make_float2(lg2_hw(u0[q].x), lg2_hw(u0[q].y)), a);
+        a = f2_fma(f2_sub(half, u1), make_float2(lg2_hw(u1.x), lg2_hw(u1.y)), a);
+    };
+    const float2 xz[2][2] = {{make_float2(pxz0.x, pxz1.x), make_float2(pxz0.y, pxz1.y)},
+                             {make_float2(pxz0.z, pxz1.z), make_float2(pxz0.w, pxz1.w)}};
+    const float2 yz[2][2] = {{make_float2(pyz0.x, pyz1.x), make_float2(pyz0.y, pyz1.y)},
+                             {make_float2(pyz0.z, pyz1.z), make_float2(pyz0.w, pyz1.w)}};
+    const float2 z2[2] = {f2_sub(f2_sub(make_float2(mz0.x, mz1.x), xz[0][0]), xz[1][0]),
+                          f2_sub(f2_sub(make_float2(mz0.y, mz1.y), xz[0][1]), xz[1][1])};
+    // the 8 counted cells and (a, b, 2)
 #pragma unroll
-    for (int q = 0; q < kCells; ++q) {
-        float2& a = acc[q < 14 ? 0 : 1];
-        const float2 us = f2_add(u0[q], u1[q]);
-        const float2 ls = make_float2(lg2_hw(us.x), lg2_hw(us.y));
-        const float2 l0 = make_float2(lg2_hw(u0[q].x), lg2_hw(u0[q].y));
-        const float2 l1 = make_float2(lg2_hw(u1[q].x), lg2_hw(u1[q].y));
-        a = f2_fma(f2_sub(us, half), ls, a);
-        // 1/2 - u: round-to-nearest is symmetric, so this is the scalar code's -(u - 1/2) exactly
-        a = f2_fma(f2_sub(half, u0[q]), l0, a);
-        a = f2_fma(f2_sub(half, u1[q]), l1, a);
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float2 c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
+            term(9 * a + 3 * b, c0);
+            term(9 * a + 3 * b + 1, c1);
+            term(9 * a + 3 * b + 2, f2_sub(f2_sub(f2_dup(rc.xy[2 * a + b]), c0), c1));
+        }
+    // (a, 2, z), then (a, 2, 2)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        float2 a2z[2];
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            a2z[z] = f2_sub(f2_sub(xz[a][z], n8[4 * a + z]), n8[4 * a + 2 + z]);
+            term(9 * a + 6 + z, a2z[z]);
+        }
+        term(9 * a + 8, f2_sub(f2_sub(f2_dup(rc.xa2[a]), a2z[0]), a2z[1]));
     }
+    // (2, b, z), then (2, b, 2); (2, 2, z); (2, 2, 2)
+    float2 c2bz[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            c2bz[b][z] = f2_sub(f2_sub(yz[b][z], n8[2 * b + z]), n8[4 + 2 * b + z]);
+            term(18 + 3 * b + z, c2bz[b][z]);
+        }
+        term(18 + 3 * b + 2, f2_sub(f2_sub(f2_dup(rc.x2b[b]), c2bz[b][0]), c2bz[b][1]));
+    }
+    float2 c22z[2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+        c22z[z] = f2_sub(f2_sub(z2[z], c2bz[0][z]), c2bz[1][z]);
+        term(24 + z, c22z[z]);
+    }
+    term(26, f2_sub(f2_sub(f2_dup(rc.c22), c22z[0]), c22z[1]));
     const float2 s = f2_add(acc[0], acc[1]);
     return make_float2(__fmaf_rn(0.6931471805599453f, s.x, -27.f * 0.9189385332046727f),
                        __fmaf_rn(0.6931471805599453f, s.y, -27.f * 0.9189385332046727f));
