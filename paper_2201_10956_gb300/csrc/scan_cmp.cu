@@ -623,9 +623,11 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                                         n8[c][4 * aa + 2 * bb + z] = __uint_as_float(bb == bme ? own : oth);
                                     }
                         cells_u(n8[0], rcl[0], tik[m][0], tjk[m][0], tmk[m][0], u0);
-                        cells_u(n8[1], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
-                        if (pruning && __fsub_rn(k2_bound_u(u0, u1), prune) > fminf(es.tloc, thr_g))
+                        if (pruning && __fsub_rn(k2_bound_stream1(u0, n8[1], rcl[1], tik[m][1], tjk[m][1],
+                                                                  tmk[m][1]),
+                                                 prune) > fminf(es.tloc, thr_g))
                             continue;
+                        cells_u(n8[1], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
                     }
                     int r0[kCells], r1[kCells];
                     if (!counts_of(u0, u1, pt.n_c[0], pt.n_c[1], r0, r1)) {

@@ -394,6 +394,61 @@ __device__ __forceinline__ float2 k2_bound_stream(const float2* u0, const float2
                        __fmaf_rn(0.6931471805599453f, s.y, -27.f * 0.9189385332046727f));
 }
 
+// k2_bound_stream for one table (plain form): class 0's cells u0 given, class 1's derived on the
+// fly from n8 (count + 1 of its 8 counted cells), the row cells and the pair-table rows.
+__device__ __forceinline__ float k2_bound_stream1(const float* u0, const float* n8, const RowCells& rc,
+                                                  float4 pxz, float4 pyz, float2 mz) {
+    float acc[2] = {0.f, 0.f};
+    auto term = [&](int q, float u1) {
+        float& a = acc[q & 1];
+        const float us = __fadd_rn(u0[q], u1);
+        a = __fmaf_rn(__fsub_rn(us, 0.5f), lg2_hw(us), a);
+        a = __fmaf_rn(__fsub_rn(0.5f, u0[q]), lg2_hw(u0[q]), a);
+        a = __fmaf_rn(__fsub_rn(0.5f, u1), lg2_hw(u1), a);
+    };
+    const float xz[2][2] = {{pxz.x, pxz.y}, {pxz.z, pxz.w}};
+    const float yz[2][2] = {{pyz.x, pyz.y}, {pyz.z, pyz.w}};
+    const float z2[2] = {__fsub_rn(__fsub_rn(mz.x, xz[0][0]), xz[1][0]),
+                         __fsub_rn(__fsub_rn(mz.y, xz[0][1]), xz[1][1])};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
+            term(9 * a + 3 * b, c0);
+            term(9 * a + 3 * b + 1, c1);
+            term(9 * a + 3 * b + 2, __fsub_rn(__fsub_rn(rc.xy[2 * a + b], c0), c1));
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        float a2z[2];
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            a2z[z] = __fsub_rn(__fsub_rn(xz[a][z], n8[4 * a + z]), n8[4 * a + 2 + z]);
+            term(9 * a + 6 + z, a2z[z]);
+        }
+        term(9 * a + 8, __fsub_rn(__fsub_rn(rc.xa2[a], a2z[0]), a2z[1]));
+    }
+    float c2bz[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            c2bz[b][z] = __fsub_rn(__fsub_rn(yz[b][z], n8[2 * b + z]), n8[4 + 2 * b + z]);
+            term(18 + 3 * b + z, c2bz[b][z]);
+        }
+        term(18 + 3 * b + 2, __fsub_rn(__fsub_rn(rc.x2b[b], c2bz[b][0]), c2bz[b][1]));
+    }
+    float c22z[2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+        c22z[z] = __fsub_rn(__fsub_rn(z2[z], c2bz[0][z]), c2bz[1][z]);
+        term(24 + z, c22z[z]);
+    }
+    term(26, __fsub_rn(__fsub_rn(rc.c22, c22z[0]), c22z[1]));
+    return __fmaf_rn(0.6931471805599453f, __fadd_rn(acc[0], acc[1]), -27.f * 0.9189385332046727f);
+}
+
 // Exact integer cells r = u - 1 of both classes; false unless every cell lies in [0, N_c]
 // (which keeps every log-factorial lookup of the table in range).
 __device__ __forceinline__ bool counts_of(const float* u0, const float* u1, int n0, int n1,
