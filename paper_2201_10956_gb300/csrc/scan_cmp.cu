@@ -562,73 +562,77 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         rcv[q][e] = __shfl_xor_sync(0xffffffffu, bme ? v[q][e] : v[q][4 + e], 1);
-                // paired form: both triplets of the lane at once (lane x of every float2 is
-                // m = 0, lane y m = 1): class 0's cells kept, class 1's derived on the fly into
-                // the bound (f32x2 instructions); survivors derive their class-1 cells again
-                float2 u0p[kCells], n8p[2][8], bnd = make_float2(0.f, 0.f);
+                // n8[c][4 a + 2 b + z] = count + 1 of triplet m (lane pair exchange undone)
+                auto n8_of = [&](int m, int c, int e) {
+                    const int q = 2 * c + (e >> 2), bb = (e >> 1) & 1, z = e & 1;
+                    const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
+                    const uint32_t oth = rcv[q][2 * m + z];
+                    return __uint_as_float(bb == bme ? own : oth);
+                };
+                // paired form: the lane's two triplets in the two lanes of f32x2 instructions
+                // (x: m = 0, y: m = 1); the inputs are gathered into lane pairs once, and the bound
+                // derives both classes' cells on the fly
+                float2 n8p[2][8], xzp[2][2][2], yzp[2][2][2], mzp[2][2], bnd = make_float2(0.f, 0.f);
                 if constexpr (kPaired) {
 #pragma unroll
-                    for (int c = 0; c < 2; ++c)
+                    for (int c = 0; c < 2; ++c) {
 #pragma unroll
-                        for (int aa = 0; aa < 2; ++aa)
-#pragma unroll
-                            for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-                                for (int z = 0; z < 2; ++z) {
-                                    const int q = 2 * c + aa;
-                                    float e[2];
-#pragma unroll
-                                    for (int m = 0; m < 2; ++m) {
-                                        const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
-                                        const uint32_t oth = rcv[q][2 * m + z];
-                                        e[m] = __uint_as_float(bb == bme ? own : oth);
-                                    }
-                                    n8p[c][4 * aa + 2 * bb + z] = make_float2(e[0], e[1]);
-                                }
-                    cells_u2(n8p[0], rcl[0], tik[0][0], tik[1][0], tjk[0][0], tjk[1][0], tmk[0][0],
-                             tmk[1][0], u0p);
-                    if (pruning)
-                        bnd = k2_bound_stream(u0p, n8p[1], rcl[1], tik[0][1], tik[1][1], tjk[0][1],
-                                              tjk[1][1], tmk[0][1], tmk[1][1]);
+                        for (int e = 0; e < 8; ++e) n8p[c][e] = make_float2(n8_of(0, c, e), n8_of(1, c, e));
+                        const float4 x0 = tik[0][c], x1 = tik[1][c], y0 = tjk[0][c], y1 = tjk[1][c];
+                        xzp[c][0][0] = make_float2(x0.x, x1.x); xzp[c][0][1] = make_float2(x0.y, x1.y);
+                        xzp[c][1][0] = make_float2(x0.z, x1.z); xzp[c][1][1] = make_float2(x0.w, x1.w);
+                        yzp[c][0][0] = make_float2(y0.x, y1.x); yzp[c][0][1] = make_float2(y0.y, y1.y);
+                        yzp[c][1][0] = make_float2(y0.z, y1.z); yzp[c][1][1] = make_float2(y0.w, y1.w);
+                        mzp[c][0] = make_float2(tmk[0][c].x, tmk[1][c].x);
+                        mzp[c][1] = make_float2(tmk[0][c].y, tmk[1][c].y);
+                    }
+                    if (pruning) {
+                        const float2 sacc = k2_bound_cells<LaneOps2>(n8p, rcl, xzp, yzp, mzp);
+                        bnd = make_float2(k2_bound_finish(sacc.x), k2_bound_finish(sacc.y));
+                    }
                 }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     const int k = kb0 + 4 * unit + 2 * bme + m;
                     if (!(jrow && k > j && k < M)) continue;
+                    // triplet m's inputs: counted cells, pair-table rows (X, Z), (Y, Z), marginal of Z
+                    float n8[2][8], xz[2][2][2], yz[2][2][2], mz[2][2];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if constexpr (kPaired) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) n8[c][e] = m ? n8p[c][e].y : n8p[c][e].x;
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                xz[c][t >> 1][t & 1] = m ? xzp[c][t >> 1][t & 1].y : xzp[c][t >> 1][t & 1].x;
+                                yz[c][t >> 1][t & 1] = m ? yzp[c][t >> 1][t & 1].y : yzp[c][t >> 1][t & 1].x;
+                            }
+                            mz[c][0] = m ? mzp[c][0].y : mzp[c][0].x;
+                            mz[c][1] = m ? mzp[c][1].y : mzp[c][1].x;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) n8[c][e] = n8_of(m, c, e);
+                            const float4 x = tik[m][c], y = tjk[m][c];
+                            xz[c][0][0] = x.x; xz[c][0][1] = x.y; xz[c][1][0] = x.z; xz[c][1][1] = x.w;
+                            yz[c][0][0] = y.x; yz[c][0][1] = y.y; yz[c][1][0] = y.z; yz[c][1][1] = y.w;
+                            mz[c][0] = tmk[m][c].x;
+                            mz[c][1] = tmk[m][c].y;
+                        }
+                    }
                     // most tables lie far above the band: prove it from the table-free
                     // approximation and skip the exact score's log-table gathers
-                    float u0[kCells], u1[kCells];
-                    if constexpr (kPaired) {
-                        if (pruning && __fsub_rn(m ? bnd.y : bnd.x, prune) > fminf(es.tloc, thr_g))
-                            continue;
-#pragma unroll
-                        for (int q = 0; q < kCells; ++q) u0[q] = m ? u0p[q].y : u0p[q].x;
-                        float n81[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) n81[e] = m ? n8p[1][e].y : n8p[1][e].x;
-                        cells_u(n81, rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
-                    } else {
-                        float n8[2][8];  // n8[c][4 a + 2 b + z] = count + 1
-#pragma unroll
-                        for (int c = 0; c < 2; ++c)
-#pragma unroll
-                            for (int aa = 0; aa < 2; ++aa)
-#pragma unroll
-                                for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-                                    for (int z = 0; z < 2; ++z) {
-                                        const int q = 2 * c + aa;
-                                        const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
-                                        const uint32_t oth = rcv[q][2 * m + z];
-                                        n8[c][4 * aa + 2 * bb + z] = __uint_as_float(bb == bme ? own : oth);
-                                    }
-                        cells_u(n8[0], rcl[0], tik[m][0], tjk[m][0], tmk[m][0], u0);
-                        if (pruning && __fsub_rn(k2_bound_stream1(u0, n8[1], rcl[1], tik[m][1], tjk[m][1],
-                                                                  tmk[m][1]),
-                                                 prune) > fminf(es.tloc, thr_g))
-                            continue;
-                        cells_u(n8[1], rcl[1], tik[m][1], tjk[m][1], tmk[m][1], u1);
+                    if (pruning) {
+                        const float bm = kPaired ? (m ? bnd.y : bnd.x)
+                                                 : k2_bound_finish(k2_bound_cells<LaneOps1>(n8, rcl, xz, yz, mz));
+                        if (__fsub_rn(bm, prune) > fminf(es.tloc, thr_g)) continue;
                     }
+                    // a survivor (or every table, without pruning): its exact cells
+                    float u0[kCells], u1[kCells];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+                        cells_u(n8[c], rcl[c], make_float4(xz[c][0][0], xz[c][0][1], xz[c][1][0], xz[c][1][1]),
+                                make_float4(yz[c][0][0], yz[c][0][1], yz[c][1][0], yz[c][1][1]),
+                                make_float2(mz[c][0], mz[c][1]), c ? u1 : u0);
                     int r0[kCells], r1[kCells];
                     if (!counts_of(u0, u1, pt.n_c[0], pt.n_c[1], r0, r1)) {
                         atomicOr(&ctrl->status, kStBadCount);

@@ -284,169 +284,98 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 f2_dup(float a) { return make_float2(a, a); }
 
-// cells_u of two tables at once (lane x, lane y) sharing the row cells of one (i, j) pair and
-// class: the same operations in the same order as cells_u, two lanes per instruction.
-__device__ __forceinline__ void cells_u2(const float2* n8, const RowCells& rc, float4 pxz0,
-                                         float4 pxz1, float4 pyz0, float4 pyz1, float2 mz0,
-                                         float2 mz1, float2* u) {
-    const float2 xz[2][2] = {{make_float2(pxz0.x, pxz1.x), make_float2(pxz0.y, pxz1.y)},
-                             {make_float2(pxz0.z, pxz1.z), make_float2(pxz0.w, pxz1.w)}};
-    const float2 yz[2][2] = {{make_float2(pyz0.x, pyz1.x), make_float2(pyz0.y, pyz1.y)},
-                             {make_float2(pyz0.z, pyz1.z), make_float2(pyz0.w, pyz1.w)}};
-    const float2 z2[2] = {f2_sub(f2_sub(make_float2(mz0.x, mz1.x), xz[0][0]), xz[1][0]),
-                          f2_sub(f2_sub(make_float2(mz0.y, mz1.y), xz[0][1]), xz[1][1])};
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const float2 c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
-            u[9 * a + 3 * b] = c0;
-            u[9 * a + 3 * b + 1] = c1;
-            u[9 * a + 3 * b + 2] = f2_sub(f2_sub(f2_dup(rc.xy[2 * a + b]), c0), c1);
-        }
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int z = 0; z < 2; ++z)
-            u[9 * a + 6 + z] = f2_sub(f2_sub(xz[a][z], u[9 * a + z]), u[9 * a + 3 + z]);
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int z = 0; z < 2; ++z)
-            u[18 + 3 * b + z] = f2_sub(f2_sub(yz[b][z], u[3 * b + z]), u[9 + 3 * b + z]);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-        u[9 * a + 8] = f2_sub(f2_sub(f2_dup(rc.xa2[a]), u[9 * a + 6]), u[9 * a + 7]);
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-        u[18 + 3 * b + 2] = f2_sub(f2_sub(f2_dup(rc.x2b[b]), u[18 + 3 * b]), u[18 + 3 * b + 1]);
-#pragma unroll
-    for (int z = 0; z < 2; ++z)
-        u[24 + z] = f2_sub(f2_sub(z2[z], u[18 + z]), u[21 + z]);
-    u[26] = f2_sub(f2_sub(f2_dup(rc.c22), u[24]), u[25]);
-}
+// Lane arithmetic for the bound of one table (float) or two tables at once (float2, f32x2
+// instructions): every lane rounds like the scalar __fadd_rn / __fsub_rn / __fmaf_rn.
+struct LaneOps1 {
+    typedef float T;
+    static __device__ __forceinline__ T add(T a, T b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ T lg(T a) { return lg2_hw(a); }
+    static __device__ __forceinline__ T dup(float a) { return a; }
+};
+struct LaneOps2 {
+    typedef float2 T;
+    static __device__ __forceinline__ T add(T a, T b) { return f2_add(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return f2_sub(a, b); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return f2_fma(a, b, c); }
+    static __device__ __forceinline__ T lg(T a) { return make_float2(lg2_hw(a.x), lg2_hw(a.y)); }
+    static __device__ __forceinline__ T dup(float a) { return f2_dup(a); }
+};
 
-// k2_bound_u of two tables (lanes x, y) with class 1's cells derived on the fly (the same
-// operations as cells_u2) and each cell's three terms chained as soon as the cell is known, so
-// that class 1's 27 cells are never live at once.  The cells enter the two chains in another
-// order than in k2_bound_u;
-// the bound's error analysis (every finished cell adds a positive amount; 82 roundings of at
-// most 2^-24 of the largest partial sum) holds for any order.
-__device__ __forceinline__ float2 k2_bound_stream(const float2* u0, const float2* n8,
-                                                  const RowCells& rc, float4 pxz0, float4 pxz1,
-                                                  float4 pyz0, float4 pyz1, float2 mz0, float2 mz1) {
-    float2 acc[2] = {f2_dup(0.f), f2_dup(0.f)};
-    const float2 half = f2_dup(0.5f);
-    auto term = [&](int q, float2 u1) {
-        float2& a = acc[q & 1];
-        const float2 us = f2_add(u0[q], u1);
-        a = f2_fma(f2_sub(us, half), make_float2(lg2_hw(us.x), lg2_hw(us.y)), a);
-        a = f2_fma(f2_sub(half, u0[q]), make_float2(lg2_hw(u0[q].x), lg2_hw(u0[q].y)), a);
-        a = f2_fma(f2_sub(half, u1), make_float2(lg2_hw(u1.x), lg2_hw(u1.y)), a);
+// The table-free bound (k2_bound_u's terms) with both classes' cells derived on the fly (the
+// operations of cells_u, per class), each cell's three terms chained as soon as both classes'
+// values are known: no 27-cell array is ever live.  n8[c][4 a + 2 b + z] = count + 1 of the
+// counted cells, xz[c][a][z] / yz[c][b][z] = pair-table entries + 3, mz[c][z] = marginal of Z
+// + 9, rc[c] = the row cells of class c.  Cells enter the two chains in derivation order; the
+// bound's error analysis (every finished cell adds a positive amount; 82 roundings of at most
+// 2^-24 of the largest partial sum) holds for any order.
+template <class L>
+__device__ __forceinline__ typename L::T k2_bound_cells(const typename L::T (*n8)[8],
+                                                        const RowCells* rc,
+                                                        const typename L::T (*xz)[2][2],
+                                                        const typename L::T (*yz)[2][2],
+                                                        const typename L::T (*mz)[2]) {
+    typedef typename L::T T;
+    T acc[2] = {L::dup(0.f), L::dup(0.f)};
+    const T half = L::dup(0.5f);
+    auto term = [&](int q, T u0, T u1) {
+        T& a = acc[q & 1];
+        const T us = L::add(u0, u1);
+        a = L::fma(L::sub(us, half), L::lg(us), a);
+        a = L::fma(L::sub(half, u0), L::lg(u0), a);
+        a = L::fma(L::sub(half, u1), L::lg(u1), a);
     };
-    const float2 xz[2][2] = {{make_float2(pxz0.x, pxz1.x), make_float2(pxz0.y, pxz1.y)},
-                             {make_float2(pxz0.z, pxz1.z), make_float2(pxz0.w, pxz1.w)}};
-    const float2 yz[2][2] = {{make_float2(pyz0.x, pyz1.x), make_float2(pyz0.y, pyz1.y)},
-                             {make_float2(pyz0.z, pyz1.z), make_float2(pyz0.w, pyz1.w)}};
-    const float2 z2[2] = {f2_sub(f2_sub(make_float2(mz0.x, mz1.x), xz[0][0]), xz[1][0]),
-                          f2_sub(f2_sub(make_float2(mz0.y, mz1.y), xz[0][1]), xz[1][1])};
-    // the 8 counted cells and (a, b, 2)
+    auto d2 = [&](T x, T y, T z) { return L::sub(L::sub(x, y), z); };
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const float2 c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
-            term(9 * a + 3 * b, c0);
-            term(9 * a + 3 * b + 1, c1);
-            term(9 * a + 3 * b + 2, f2_sub(f2_sub(f2_dup(rc.xy[2 * a + b]), c0), c1));
+            const int e = 4 * a + 2 * b;
+            term(9 * a + 3 * b, n8[0][e], n8[1][e]);
+            term(9 * a + 3 * b + 1, n8[0][e + 1], n8[1][e + 1]);
+            term(9 * a + 3 * b + 2, d2(L::dup(rc[0].xy[2 * a + b]), n8[0][e], n8[0][e + 1]),
+                 d2(L::dup(rc[1].xy[2 * a + b]), n8[1][e], n8[1][e + 1]));
         }
-    // (a, 2, z), then (a, 2, 2)
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        float2 a2z[2];
+        T a2z[2][2];  // [class][z]
 #pragma unroll
         for (int z = 0; z < 2; ++z) {
-            a2z[z] = f2_sub(f2_sub(xz[a][z], n8[4 * a + z]), n8[4 * a + 2 + z]);
-            term(9 * a + 6 + z, a2z[z]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) a2z[c][z] = d2(xz[c][a][z], n8[c][4 * a + z], n8[c][4 * a + 2 + z]);
+            term(9 * a + 6 + z, a2z[0][z], a2z[1][z]);
         }
-        term(9 * a + 8, f2_sub(f2_sub(f2_dup(rc.xa2[a]), a2z[0]), a2z[1]));
+        term(9 * a + 8, d2(L::dup(rc[0].xa2[a]), a2z[0][0], a2z[0][1]),
+             d2(L::dup(rc[1].xa2[a]), a2z[1][0], a2z[1][1]));
     }
-    // (2, b, z), then (2, b, 2); (2, 2, z); (2, 2, 2)
-    float2 c2bz[2][2];
+    T c2bz[2][2][2];  // [class][b][z]
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
 #pragma unroll
         for (int z = 0; z < 2; ++z) {
-            c2bz[b][z] = f2_sub(f2_sub(yz[b][z], n8[2 * b + z]), n8[4 + 2 * b + z]);
-            term(18 + 3 * b + z, c2bz[b][z]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) c2bz[c][b][z] = d2(yz[c][b][z], n8[c][2 * b + z], n8[c][4 + 2 * b + z]);
+            term(18 + 3 * b + z, c2bz[0][b][z], c2bz[1][b][z]);
         }
-        term(18 + 3 * b + 2, f2_sub(f2_sub(f2_dup(rc.x2b[b]), c2bz[b][0]), c2bz[b][1]));
+        term(18 + 3 * b + 2, d2(L::dup(rc[0].x2b[b]), c2bz[0][b][0], c2bz[0][b][1]),
+             d2(L::dup(rc[1].x2b[b]), c2bz[1][b][0], c2bz[1][b][1]));
     }
-    float2 c22z[2];
+    T c22z[2][2];  // [class][z]
 #pragma unroll
     for (int z = 0; z < 2; ++z) {
-        c22z[z] = f2_sub(f2_sub(z2[z], c2bz[0][z]), c2bz[1][z]);
-        term(24 + z, c22z[z]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const T z2 = d2(mz[c][z], xz[c][0][z], xz[c][1][z]);   // #(X = 2, Z = z) + 3
+            c22z[c][z] = d2(z2, c2bz[c][0][z], c2bz[c][1][z]);
+        }
+        term(24 + z, c22z[0][z], c22z[1][z]);
     }
-    term(26, f2_sub(f2_sub(f2_dup(rc.c22), c22z[0]), c22z[1]));
-    const float2 s = f2_add(acc[0], acc[1]);
-    return make_float2(__fmaf_rn(0.6931471805599453f, s.x, -27.f * 0.9189385332046727f),
-                       __fmaf_rn(0.6931471805599453f, s.y, -27.f * 0.9189385332046727f));
+    term(26, d2(L::dup(rc[0].c22), c22z[0][0], c22z[0][1]), d2(L::dup(rc[1].c22), c22z[1][0], c22z[1][1]));
+    return L::add(acc[0], acc[1]);  // in log2 units, before the final scale and offset
 }
-
-// k2_bound_stream for one table (plain form): class 0's cells u0 given, class 1's derived on the
-// fly from n8 (count + 1 of its 8 counted cells), the row cells and the pair-table rows.
-__device__ __forceinline__ float k2_bound_stream1(const float* u0, const float* n8, const RowCells& rc,
-                                                  float4 pxz, float4 pyz, float2 mz) {
-    float acc[2] = {0.f, 0.f};
-    auto term = [&](int q, float u1) {
-        float& a = acc[q & 1];
-        const float us = __fadd_rn(u0[q], u1);
-        a = __fmaf_rn(__fsub_rn(us, 0.5f), lg2_hw(us), a);
-        a = __fmaf_rn(__fsub_rn(0.5f, u0[q]), lg2_hw(u0[q]), a);
-        a = __fmaf_rn(__fsub_rn(0.5f, u1), lg2_hw(u1), a);
-    };
-    const float xz[2][2] = {{pxz.x, pxz.y}, {pxz.z, pxz.w}};
-    const float yz[2][2] = {{pyz.x, pyz.y}, {pyz.z, pyz.w}};
-    const float z2[2] = {__fsub_rn(__fsub_rn(mz.x, xz[0][0]), xz[1][0]),
-                         __fsub_rn(__fsub_rn(mz.y, xz[0][1]), xz[1][1])};
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const float c0 = n8[4 * a + 2 * b], c1 = n8[4 * a + 2 * b + 1];
-            term(9 * a + 3 * b, c0);
-            term(9 * a + 3 * b + 1, c1);
-            term(9 * a + 3 * b + 2, __fsub_rn(__fsub_rn(rc.xy[2 * a + b], c0), c1));
-        }
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        float a2z[2];
-#pragma unroll
-        for (int z = 0; z < 2; ++z) {
-            a2z[z] = __fsub_rn(__fsub_rn(xz[a][z], n8[4 * a + z]), n8[4 * a + 2 + z]);
-            term(9 * a + 6 + z, a2z[z]);
-        }
-        term(9 * a + 8, __fsub_rn(__fsub_rn(rc.xa2[a], a2z[0]), a2z[1]));
-    }
-    float c2bz[2][2];
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-#pragma unroll
-        for (int z = 0; z < 2; ++z) {
-            c2bz[b][z] = __fsub_rn(__fsub_rn(yz[b][z], n8[2 * b + z]), n8[4 + 2 * b + z]);
-            term(18 + 3 * b + z, c2bz[b][z]);
-        }
-        term(18 + 3 * b + 2, __fsub_rn(__fsub_rn(rc.x2b[b], c2bz[b][0]), c2bz[b][1]));
-    }
-    float c22z[2];
-#pragma unroll
-    for (int z = 0; z < 2; ++z) {
-        c22z[z] = __fsub_rn(__fsub_rn(z2[z], c2bz[0][z]), c2bz[1][z]);
-        term(24 + z, c22z[z]);
-    }
-    term(26, __fsub_rn(__fsub_rn(rc.c22, c22z[0]), c22z[1]));
-    return __fmaf_rn(0.6931471805599453f, __fadd_rn(acc[0], acc[1]), -27.f * 0.9189385332046727f);
+__device__ __forceinline__ float k2_bound_finish(float s) {
+    return __fmaf_rn(0.6931471805599453f, s, -27.f * 0.9189385332046727f);
 }
 
 // Exact integer cells r = u - 1 of both classes; false unless every cell lies in [0, N_c]
