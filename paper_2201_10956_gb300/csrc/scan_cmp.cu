@@ -112,9 +112,12 @@ struct MaskWord {
     uint4 q[4];
 };
 
-// CTA (b, i - i0, c), 128 threads: thread r writes row r = 2 (m - 64 b) + z of every chunk of
-// block b for the two sets (c, 0) and (c, 1) of first SNP i: the bits [g_m = z] of the class-c
-// samples with g_i = a, in sample order, then the bias sample, then zeros to the set's K-steps.
+// Rows of a chunk come in 16-row groups: row 16 G + 8 z + r holds SNP m = 64 b + 8 G + r with
+// genotype z (8 SNPs of genotype 0, then the same 8 of genotype 1), so that a 16x256b
+// tensor-memory load hands a thread both genotype rows of one SNP (see the epilogue).
+// CTA (b, i - i0, c), 128 threads: thread r writes row r of every chunk of block b for the two
+// sets (c, 0) and (c, 1) of first SNP i: the bits [g_m = z] of the class-c samples with
+// g_i = a, in sample order, then the bias sample, then zeros to the set's K-steps.
 // Plane words come four at a time (one 16-byte load per 128 samples, the next one in flight
 // while the current one is compressed); each word's masks of both sets come in four 16-byte
 // shared-memory loads.
@@ -131,8 +134,8 @@ compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* 
     const int ks0 = fp->ks[2 * c], ks1 = fp->ks[2 * c + 1];
     const long long fb0 = fp->base[2 * c], fb1 = fp->base[2 * c + 1];
     const int M = pl.M;
-    const int r = threadIdx.x, z = r & 1;
-    const int m = 64 * b + (r >> 1);
+    const int r = threadIdx.x, z = (r >> 3) & 1;
+    const int m = 64 * b + 8 * (r >> 4) + (r & 7);
     const long long coff = c ? pl.coff[1] : pl.coff[0];
     const int W4 = c ? pl.W4[1] : pl.W4[0];
     const int W = 4 * W4;                       // 32-sample words of the class
@@ -209,6 +212,9 @@ constexpr uint32_t kCmpSfCol = 480;      // block scales: A at 480..495, B at 49
 constexpr int kCmpThreads = 512;
 constexpr int kCmpEpiWarp0 = 4, kCmpEpiWarps = 12, kCmpEpiThreads = kCmpEpiWarps * 32;
 constexpr int kCmpEpiParts = kCmpEpiWarps / 4;   // epilogue warps per tensor-memory lane quadrant
+// the epilogue's items: per quadrant 2 lane groups (8 second SNPs each) x 4 column groups (8 third
+// SNPs each), split 3 / 3 / 2 over its three warps
+static_assert(kCmpEpiParts == 3 && kTJ == 4 * 2 * 8 && kTK == 4 * 8, "epilogue item split");
 constexpr int kCmpRegLaunch = 128, kCmpRegCtl = 56, kCmpRegEpi = 152;
 static_assert(kCmpRegCtl + 3 * kCmpRegEpi == 4 * kCmpRegLaunch, "register split");
 static_assert(kCmpThreads * kCmpRegLaunch == 65536, "the launch holds the whole register file");
@@ -228,10 +234,11 @@ __device__ __forceinline__ void mma_ss_mx_elect(uint32_t d, uint64_t a, uint64_t
         ::"r"(d), "l"(a), "l"(b), "r"(acc), "r"(sfa), "r"(sfb), "r"(kIdescCmp) : "memory");
 }
 
-// 8 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t* v) {
+// 16 lanes x 16 FP32 columns from taddr: thread t gets lane t / 4 (v[0..1]) and lane t / 4 + 8
+// (v[2..3]) at columns 2 (t % 4) + {0, 1}, then the same at columns + 8 (v[4..7]).
+__device__ __forceinline__ void tc_ld16x2(uint32_t taddr, uint32_t* v) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        "tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
           "=r"(v[7])
         : "r"(taddr));
@@ -478,13 +485,16 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kCmpRegEpi));
         // ------------------------------------------------ epilogue
-        // tensor-memory lane L = 2 jl + b holds, per set (c, a), the counts + 1 of
-        // (i = a, j = b, k = z) in columns 2 kl + z; the lane pair (b = 0, 1) of one jl swaps
-        // halves so that each lane holds all 8 cells of two triplets per 4-column group.
+        // Per set (c, a), tensor-memory lane 16 G + 8 b + r holds the counts + 1 of second SNP
+        // jl = 8 G + r with genotype b, in column 16 H + 8 z + s for third SNP kl = 8 H + s with
+        // genotype z (the chunks' row order).  A 16x256b.x2 load at lane group G, column group H
+        // gives thread t the cells (b, z) of jl = 8 G + t / 4 and kl = 8 H + 2 (t % 4) + e,
+        // e = 0, 1, in registers 4 z + 2 b + e: all 8 cells of a set for two triplets.  Items of
+        // a quadrant: lane groups G = 2 quad + h (h = 0, 1) x column groups H = 0..3; part 0
+        // takes h = 0 with H = 0..2, part 1 h = 1 with H = 0..2, part 2 both h with H = 3.
         const int tid = threadIdx.x - kCmpEpiWarp0 * 32;     // 0 .. 383
         const int quad = warp & 3, part = (warp - kCmpEpiWarp0) >> 2;
-        const int jl = 16 * quad + (lane >> 1), bme = lane & 1;
-        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        const int trow = lane >> 2, tcol = 2 * (lane & 3);
         const int M = cd.pl.M;
         const PairTables pt = cd.pt;
         const float2* lf2 = cd.k2.lf2;
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
         Ring rR{0, 0u};
         for (long long tl = 0; tl < my_tiles; ++tl) {
             const CmpTile T = cmp_tile(a, blockIdx.x + tl * gridDim.x);
-            const int i = a.i0 + T.f, j = kTJ * T.jb + jl, kb0 = kTK * T.kb;
+            const int i = a.i0 + T.f, kb0 = kTK * T.kb;
             bool bad = false;
             if (tid == 0) {
                 bad = !mbar_wait_t(accF0 + 8 * (int)(tl & 1), (unsigned)((tl >> 1) & 1), abort_flag,
@@ -514,32 +524,42 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                 regs[q] = rR.s;
                 ring_next(rR, kCmpRegions);
             }
-            long long pij = -1;
-            if (j < M && j > i) {
-                pij = pair_index(i, j);
-                if (pij < cd.pair_begin || pij >= cd.pair_end) pij = -1;
-            }
-            const bool jrow = pij >= 0;
-            int4 pxy[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
-            int2 my[2] = {make_int2(0, 0), make_int2(0, 0)}, mx[2];
-            if (jrow) {
-                pxy[0] = __ldg(pt.pt + pij);
-                pxy[1] = __ldg(pt.pt + pt.n_pairs + pij);
-                my[0] = __ldg(pt.marg + j);
-                my[1] = __ldg(pt.marg + M + j);
-            }
+            int2 mx[2];
             mx[0] = __ldg(pt.marg + i);
             mx[1] = __ldg(pt.marg + M + i);
-            const RowCells rcl[2] = {row_cells(pxy[0], mx[0], my[0], pt.n_c[0]),
-                                     row_cells(pxy[1], mx[1], my[1], pt.n_c[1])};
-            for (int unit = part; unit < kTK / 4; unit += kCmpEpiParts) {
+            int cur_h = -1, j = 0;
+            bool jrow = false;
+            RowCells rcl[2];
+            const int n_items = part == 2 ? 2 : 3;
+            for (int it = 0; it < n_items; ++it) {
+                const int h = part == 2 ? it : part, H = part == 2 ? 3 : it;
+                if (h != cur_h) {  // this thread's second SNP and its row cells
+                    cur_h = h;
+                    j = kTJ * T.jb + 8 * (2 * quad + h) + trow;
+                    long long pij = -1;
+                    if (j < M && j > i) {
+                        pij = pair_index(i, j);
+                        if (pij < cd.pair_begin || pij >= cd.pair_end) pij = -1;
+                    }
+                    jrow = pij >= 0;
+                    int4 pxy[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+                    int2 my[2] = {make_int2(0, 0), make_int2(0, 0)};
+                    if (jrow) {
+                        pxy[0] = __ldg(pt.pt + pij);
+                        pxy[1] = __ldg(pt.pt + pt.n_pairs + pij);
+                        my[0] = __ldg(pt.marg + j);
+                        my[1] = __ldg(pt.marg + M + j);
+                    }
+                    rcl[0] = row_cells(pxy[0], mx[0], my[0], pt.n_c[0]);
+                    rcl[1] = row_cells(pxy[1], mx[1], my[1], pt.n_c[1]);
+                }
                 const float thr_g = __uint_as_float(*(volatile unsigned*)&ctrl->thr);
-                // this lane's two triplets: k = kb0 + 4 unit + 2 bme + m; pair-table rows first
+                // this thread's two triplets: k = kb0 + 8 H + tcol + m; pair-table rows first
                 float4 tik[2][2], tjk[2][2];
                 float2 tmk[2][2];
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
-                    const int k = kb0 + 4 * unit + 2 * bme + m;
+                    const int k = kb0 + 8 * H + tcol + m;
                     const bool val = jrow && k > j && k < M;
                     const long long pik = val ? pair_index(i, k) : 0, pjk = val ? pair_index(j, k) : 0;
                     const int kq = val ? k : 0;
@@ -553,21 +573,12 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                 uint32_t v[kCmpSets][8];
 #pragma unroll
                 for (int q = 0; q < kCmpSets; ++q)
-                    tc_ld8(tmem + lane_base + (uint32_t)(regs[q] * kN + 8 * unit), v[q]);
+                    tc_ld16x2(tmem + ((uint32_t)(32 * quad + 16 * h) << 16) + (uint32_t)(regs[q] * kN + 16 * H),
+                              v[q]);
                 tc_wait_ld();
-                // columns 8 unit + e: kl = e / 2, z = e % 2; lane bme keeps kl 2 bme, 2 bme + 1
-                uint32_t rcv[kCmpSets][4];
-#pragma unroll
-                for (int q = 0; q < kCmpSets; ++q)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        rcv[q][e] = __shfl_xor_sync(0xffffffffu, bme ? v[q][e] : v[q][4 + e], 1);
-                // n8[c][4 a + 2 b + z] = count + 1 of triplet m (lane pair exchange undone)
+                // n8[c][4 a + 2 b + z] = count + 1 of triplet m: set 2 c + a, register 4 z + 2 b + m
                 auto n8_of = [&](int m, int c, int e) {
-                    const int q = 2 * c + (e >> 2), bb = (e >> 1) & 1, z = e & 1;
-                    const uint32_t own = bme ? v[q][4 + 2 * m + z] : v[q][2 * m + z];
-                    const uint32_t oth = rcv[q][2 * m + z];
-                    return __uint_as_float(bb == bme ? own : oth);
+                    return __uint_as_float(v[2 * c + (e >> 2)][4 * (e & 1) + 2 * ((e >> 1) & 1) + m]);
                 };
                 // paired form: the lane's two triplets in the two lanes of f32x2 instructions
                 // (x: m = 0, y: m = 1); the inputs are gathered into lane pairs once, and the bound
@@ -593,7 +604,7 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                 }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
-                    const int k = kb0 + 4 * unit + 2 * bme + m;
+                    const int k = kb0 + 8 * H + tcol + m;
                     if (!(jrow && k > j && k < M)) continue;
                     // triplet m's inputs: counted cells, pair-table rows (X, Z), (Y, Z), marginal of Z
                     float n8[2][8], xz[2][2][2], yz[2][2][2], mz[2][2];
