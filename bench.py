@@ -48,8 +48,6 @@ L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
 # an entry is removed whenever that kernel changes.
 TRAFFIC = {
     ("mma4", "large"): 567.59e6 + 7.07e6,   # scan_mma_kernel<e2m1> (plain form), 2048 x 16384
-    # scan_cmp_kernel, 2048 x 16384, 2 GiB ranges: mean DRAM read + write of two launches
-    ("mma4c", "large"): (5366121216 + 7884800 + 4828321536 + 1882880) / 2,
 }
 
 
@@ -152,12 +150,14 @@ DTYPES = {1: "u32 popc / int32 counts", 2: "u32 popc / int32 counts",
 
 
 def compacted_fraction(genotypes):
-    """Share of sample-triplets (i < j < k, all samples) whose first SNP i has genotype 0 or 1,
-    i.e. the samples the compacted tensor form multiplies."""
+    """Share of sample-triplets (i < j < k, all samples) that the compacted tensor form
+    multiplies: those whose first SNP i has one of its two counted genotypes (the most frequent
+    genotype of SNP i over all samples is derived, not counted)."""
     m, n = genotypes.shape
-    not2 = (genotypes != 2).sum(axis=1).astype(np.float64)          # per SNP
+    most = np.max(np.stack([(genotypes == v).sum(axis=1) for v in range(3)]), axis=0)
+    counted = (n - most).astype(np.float64)                          # per SNP
     later_pairs = np.array([(m - i - 1) * (m - i - 2) / 2 for i in range(m)])
-    return float((not2 * later_pairs).sum() / (gen.n_triplets(m) * n))
+    return float((counted * later_pairs).sum() / (gen.n_triplets(m) * n))
 
 
 def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config, cmp_frac=1.0):
@@ -173,9 +173,9 @@ def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config, cmp_frac=1.0):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     traffic = TRAFFIC.get((PATH_NAMES.get(path), config))
     if path == 6:
-        # sample-compacted form: 4 MACs per (triplet, sample with g_i in {0, 1}); cmp_frac is
-        # the share of sample-triplets whose first-SNP genotype is 0 or 1 (the others enter no
-        # set), computed from the data set
+        # sample-compacted form: 4 MACs per (triplet, sample with a counted g_i); cmp_frac is
+        # the share of sample-triplets whose first-SNP genotype is a counted one (the samples of
+        # the derived genotype enter no set), computed from the data set
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         peak = bf16 * 6.0
         achieved = units * cmp_frac * 8.0 / kern_s / 1e12
@@ -183,8 +183,9 @@ def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config, cmp_frac=1.0):
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst) x 6 (e2m1/bf16 nominal ratio)",
-                "work_note": f"8 FLOP (4 useful 0/1 MACs) per sample-triplet with a first-SNP "
-                             f"genotype in {{0,1}} ({cmp_frac:.4f} of all); tile waste excluded"}
+                "work_note": f"8 FLOP (4 useful 0/1 MACs) per sample-triplet whose first-SNP "
+                             f"genotype is one of its two counted ones ({cmp_frac:.4f} of all); "
+                             f"tile waste excluded"}
     if path in (3, 4, 5):
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         ratio, elem = {3: (2.0, "e4m3"), 4: (1.0, "f16"), 5: (6.0, "e2m1")}[path]
@@ -321,7 +322,7 @@ def run_batch(args, rank, world, local_rank):
     peaks = read_peaks()
     kern_s = statistics.mean(kern_ms) / 1000.0
     # tensor work: 16 FLOP per sample-triplet of the one-hot cohorts, 8 per sample-triplet with a
-    # first-SNP genotype in {0,1} of the compacted ones
+    # counted first-SNP genotype of the compacted ones
     flop = sum(gen.n_triplets(d.n_snps) * d.n_samples * 16.0 for d, p in zip(cohorts, paths) if p == 5)
     flop += sum(gen.n_triplets(d.n_snps) * d.n_samples * 8.0 * compacted_fraction(d.genotypes)
                 for d, p in zip(cohorts, paths) if p == 6)

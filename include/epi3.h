@@ -54,13 +54,15 @@ extern "C" {
                              (tcgen05 kind::f8f6f4, FP32 accumulation), 19 derived */
 #define EPI3_PATH_MMA16 4 /* the same GEMM with FP16 operands (tcgen05 kind::f16) */
 #define EPI3_PATH_MMA4 5  /* the same GEMM with FP4 E2M1 operands, two per byte, every 32-element
-                             block scaled by 2^0 (tcgen05 kind::mxf4, FP32 accumulation); the
-                             default (auto) scan path up to about 8700 SNPs, POPC8 beyond */
-#define EPI3_PATH_MMA4C 6 /* the 8 cells on sample-compacted FP4 E2M1 operands: per first SNP i,
-                             class and genotype a of i, the samples with g_i = a are gathered
-                             once, and n(a, b, z) = (one-hot rows (j, b)) x (one-hot rows (k, z))
-                             over those samples (tcgen05 kind::mxf4, both operands from shared
-                             memory, 4 MACs per sample-triplet); 19 cells derived */
+                             block scaled by 2^0 (tcgen05 kind::mxf4, FP32 accumulation); its
+                             tile list serves up to 9377 SNPs (EPI3_ERR_UNSUPPORTED beyond) */
+#define EPI3_PATH_MMA4C 6 /* 8 cells on sample-compacted FP4 E2M1 operands: per first SNP i, its
+                             two least frequent genotypes a are counted (the third is derived
+                             with the other 19 cells); per class and counted a the samples with
+                             g_i = a are gathered once, and n(a, b, z) = (one-hot rows (j, b)) x
+                             (one-hot rows (k, z)) over those samples (tcgen05 kind::mxf4, both
+                             operands from shared memory, 4 MACs per counted sample-triplet);
+                             any number of SNPs */
 
 #define EPI3_MAX_TOPK 512
 
@@ -204,7 +206,7 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
 /*
  * Options (strings): "path" = "auto" (the default: the form a tuner measures fastest for the
  * shape, among EPI3_PATH_POPC8, EPI3_PATH_MMA4C and both forms of EPI3_PATH_MMA4 (which serves
- * up to about 8700 SNPs); the first auto scan of a (n_snps / 64, n_samples / 1024) bucket
+ * up to 9377 SNPs); the first auto scan of a (n_snps / 64, n_samples / 1024) bucket
  * times each on the heaviest slice of pairs, at most 1/16 of them, and the choice is kept for
  * the process and appended to the file named by the environment variable EPI3_TUNE_CACHE,
  * if set, for later processes) | "popc" | "popc8" | "mma" | "mma16" | "mma4" | "mma4c";

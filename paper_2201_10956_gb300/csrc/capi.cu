@@ -688,11 +688,17 @@ void plan_cmp(const epi3_handle* h, long long pb, long long pe, CmpPlan& P) {
         CmpFirst& f = firsts[i];
         f.b_lo = std::max((i + 1) / 64, jb_first);
         f.jb_end = jb_end;
+        // the two least frequent genotypes of SNP i are counted, the third derived
+        int n[2][3];
+        for (int c = 0; c < 2; ++c) {
+            const int2 mg = h->h_marg[(size_t)c * M + i];
+            n[c][0] = mg.x;
+            n[c][1] = mg.y;
+            n[c][2] = (c ? h->N1 : h->N0) - mg.x - mg.y;
+        }
+        f.drop = cmp_drop(n[0][0] + n[1][0], n[0][1] + n[1][1], n[0][2] + n[1][2]);
         for (int c = 0; c < 2; ++c)
-            for (int a = 0; a < 2; ++a) {
-                const int2 mg = h->h_marg[(size_t)c * M + i];
-                f.ks[2 * c + a] = (a == 0 ? mg.x : mg.y) / 256 + 1;  // + the bias sample
-            }
+            for (int s = 0; s < 2; ++s) f.ks[2 * c + s] = n[c][cmp_geno(f.drop, s)] / 256 + 1;  // + the bias sample
         const long long ch = cmp_chunks_of(f, M);
         if (range_start.empty() || (size_t)(chunks + ch) * 16384 > h->cmp_cap ||
             i - range_start.back() >= 65535) {

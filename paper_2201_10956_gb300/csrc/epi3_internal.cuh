@@ -179,12 +179,16 @@ struct CohortDev {
 };
 
 // ---------------------------------------------------------------- sample-compacted tensor scan
-constexpr int kCmpSets = 4;      // (class, genotype 0/1 of the first SNP)
+constexpr int kCmpSets = 4;      // (class, one of the two counted genotypes of the first SNP)
 // Per first SNP of a compaction range: the chunk index of (block b_lo, step 0) of each set and
-// the sets' K-steps; chunk (b, ks) of set q is base[q] + (b - b_lo) * ks[q] + ks.
+// the sets' K-steps; chunk (b, ks) of set q is base[q] + (b - b_lo) * ks[q] + ks.  The first
+// SNP's most frequent genotype (over both classes) is derived, not counted: set 2 c + s holds
+// the class-c samples whose first-SNP genotype is cmp_geno(drop, s).  Both classes derive the
+// same genotype, so that every cell of one class meets the same cell of the other.
 struct CmpFirst {
     long long base[kCmpSets];
     int ks[kCmpSets];
+    int drop;
     int b_lo;                    // first 64-SNP block compacted: the first j block of the tiles
     int tiles;                   // tiles of this first SNP
     int jb_end;                  // one past its last j block (the pair range's last j)
@@ -199,6 +203,16 @@ struct CmpArgs {
     const uint8_t* cmp;          // compacted chunks of the range
     unsigned long long* prof;    // optional (instrumented kernel): wait cycles per role
 };
+// The genotype counted in slot s (0, 1) when genotype d is derived: the other two, ascending.
+__host__ __device__ __forceinline__ int cmp_geno(int d, int s) {
+    return s == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);
+}
+// The genotype derived: the most frequent one (ties: 2, then 0), so that the two counted sets
+// are the smallest; n0, n1, n2 = counts of genotypes 0, 1, 2 over both classes.
+inline int cmp_drop(int n0, int n1, int n2) {
+    if (n2 >= n0 && n2 >= n1) return 2;
+    return n0 >= n1 ? 0 : 1;
+}
 // compacted chunks of one first SNP: 16 KB each
 inline long long cmp_chunks_of(const CmpFirst& f, int M) {
     const long long nblk = (M + 63) / 64 - f.b_lo;

@@ -1,17 +1,21 @@
 // Tensor-core counting scan on sample-compacted operands (path EPI3_PATH_MMA4C).
 //
-// For a fixed first SNP i, class c and genotype a in {0, 1} of SNP i, let S be the samples of
-// class c with g_i = a.  The 8 cells with genotypes in {0,1} of every triplet (i, j, k) are
+// For a fixed first SNP i, class c and genotype a of SNP i, let S be the samples of class c
+// with g_i = a.  The cells (a, b, z) with b, z in {0,1} of every triplet (i, j, k) are
 //     n(a, b, z) = sum over s in S of [g_j(s) = b] [g_k(s) = z],
-// a plain GEMM of two one-hot matrices over the samples of S: rows (j, b) x columns (k, z).  So
-// the samples of each of the four sets (c, a) are gathered once per first SNP ("compaction":
-// bit extraction from the packed planes, expansion to FP4 E2M1 0/1 values in the 128B-swizzled
-// shared-memory image), and the scan multiplies compacted chunks straight from L2: both MMA
-// operands come from shared memory, filled by bulk copies, with no operand formed on chip and
-// 4 MACs per sample-triplet (the samples with g_i = 2 enter no set).  The 19 other cells follow
-// from pair tables and marginals, then K2 and the candidate band exactly as in the other scans
-// (Eq. 1; the paper counts with POPCNT, Sec. IV, and points at tensor-core formulations in
-// Sec. II).
+// a plain GEMM of two one-hot matrices over the samples of S: rows (j, b) x columns (k, z).  Two
+// genotypes a of SNP i are counted this way, the two least frequent over all samples; the most
+// frequent one is derived with the other 19 cells (the same genotype in both classes), so the
+// GEMMs run over the smallest share of the samples.  The samples of each of the four sets
+// (c, a) are gathered once per first SNP ("compaction": bit extraction from the packed planes,
+// expansion to FP4 E2M1 0/1 values in the 128B-swizzled shared-memory image), and the scan
+// multiplies compacted chunks straight from L2: both MMA operands come from shared memory,
+// filled by bulk copies, with no operand formed on chip and 4 MACs per sample-triplet whose
+// first-SNP genotype is counted.  The epilogue relabels SNP i's genotypes (counted ones 0 and 1,
+// the derived one 2) in its pair-table and marginal inputs, derives the 19 other cells from pair
+// tables and marginals, and restores the genotype order before the exact table is scored: K2
+// and the candidate band exactly as in the other scans (Eq. 1; the paper counts with POPCNT,
+// Sec. IV, and points at tensor-core formulations in Sec. II).
 //
 // Every set carries one bias sample (a 1 in every row) after its samples, so every accumulator
 // ends at count + 1, the argument of the epilogue's count + 1 arithmetic.
@@ -95,6 +99,43 @@ __device__ __forceinline__ void cmp_push(uint8_t* set_base, uint8_t* slab, int r
     }
 }
 
+// A first SNP whose derived genotype d is not 2 counts the other two: slot s = 0, 1 holds
+// genotype cmp_geno(d, s) and the derived genotype takes label 2 (in both classes alike), so
+// the epilogue's inclusion-exclusion and bound run unchanged on relabelled inputs (every value
+// an exact integer; the bound is a sum over cells, each cell pairing its two classes).
+// Pair table (X = first SNP, Y) of a class, n(a, b) at 2 a + b, with Y's marginal.
+__device__ __forceinline__ int4 relabel_xy(int4 p, int2 my, int d) {
+    const int n20 = my.x - p.x - p.z, n21 = my.y - p.y - p.w;
+    return d == 0 ? make_int4(p.z, p.w, n20, n21) : d == 1 ? make_int4(p.x, p.y, n20, n21) : p;
+}
+// Marginal of the first SNP (#0, #1) in a class of nc samples.
+__device__ __forceinline__ int2 relabel_marg(int2 m, int nc, int d) {
+    const int n2 = nc - m.x - m.y;
+    return d == 0 ? make_int2(m.y, n2) : d == 1 ? make_int2(m.x, n2) : m;
+}
+// FP32 pair-table row (X, Z) (+ 3 each, index 2 a + z) with Z's marginal + 9.
+__device__ __forceinline__ float4 relabel_xz(float4 x, float2 mz9, int d) {
+    if (d == 2) return x;
+    const float r0 = __fsub_rn(__fsub_rn(mz9.x, x.x), x.z), r1 = __fsub_rn(__fsub_rn(mz9.y, x.y), x.w);
+    return d == 0 ? make_float4(x.z, x.w, r0, r1) : make_float4(x.x, x.y, r0, r1);
+}
+// Cells u[9 a + 3 b + z] of relabelled first-SNP genotypes back in genotype order.
+__device__ __forceinline__ void canon_rows(float* u, int d) {
+    if (d == 2) return;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const float r0 = u[e], r1 = u[9 + e], r2 = u[18 + e];   // slot 0, slot 1, derived
+        if (d == 0) {            // genotypes 1, 2, 0
+            u[e] = r2;
+            u[9 + e] = r0;
+            u[18 + e] = r1;
+        } else {                 // genotypes 0, 2, 1
+            u[9 + e] = r2;
+            u[18 + e] = r1;
+        }
+    }
+}
+
 constexpr int kCompactThreads = 128;     // one row (SNP, genotype) of the 64-SNP block per thread
 
 // Push the bits of one 32-sample word selected by a set's mask: compress by the mask (Hacker's
@@ -116,8 +157,9 @@ struct MaskWord {
 // genotype z (8 SNPs of genotype 0, then the same 8 of genotype 1), so that a 16x256b
 // tensor-memory load hands a thread both genotype rows of one SNP (see the epilogue).
 // CTA (b, i - i0, c), 128 threads: thread r writes row r of every chunk of block b for the two
-// sets (c, 0) and (c, 1) of first SNP i: the bits [g_m = z] of the class-c samples with
-// g_i = a, in sample order, then the bias sample, then zeros to the set's K-steps.
+// sets (c, 0) and (c, 1) of first SNP i: the bits [g_m = z] of the class-c samples whose g_i is
+// the set's counted genotype, in sample order, then the bias sample, then zeros to the set's
+// K-steps.
 // Plane words come four at a time (one 16-byte load per 128 samples, the next one in flight
 // while the current one is compressed); each word's masks of both sets come in four 16-byte
 // shared-memory loads.
@@ -133,12 +175,14 @@ compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* 
     if (b < b_lo) return;  // whole CTA: no block before the first SNP's successors
     const int ks0 = fp->ks[2 * c], ks1 = fp->ks[2 * c + 1];
     const long long fb0 = fp->base[2 * c], fb1 = fp->base[2 * c + 1];
+    const int drop = fp->drop;
     const int M = pl.M;
     const int r = threadIdx.x, z = (r >> 3) & 1;
     const int m = 64 * b + 8 * (r >> 4) + (r & 7);
     const long long coff = c ? pl.coff[1] : pl.coff[0];
     const int W4 = c ? pl.W4[1] : pl.W4[0];
     const int W = 4 * W4;                       // 32-sample words of the class
+    const int Nc = 128 * W4 - (c ? pl.pad[1] : pl.pad[0]);
     uint8_t* const base0 = cmp + (size_t)(fb0 + (long long)(b - b_lo) * ks0) * kCmpChunk;
     uint8_t* const base1 = cmp + (size_t)(fb1 + (long long)(b - b_lo) * ks1) * kCmpChunk;
     CmpStream s0{0ull, 0, 0}, s1{0ull, 0, 0};   // sets (c, 0) and (c, 1)
@@ -153,8 +197,15 @@ compact_kernel(Planes pl, const CmpFirst* __restrict__ firsts, int i0, uint8_t* 
         for (int w = threadIdx.x; w < nw; w += blockDim.x) {
             // word w0 + w of planes 0 and 1 of SNP i: group (w0 + w) / 4, word (w0 + w) % 4
             const int ww = w0 + w;
-            const uint32_t mk0 = prow[((size_t)(ww >> 2) * M + i) * 4 + (ww & 3)];
-            const uint32_t mk1 = prow[((size_t)(W4 + (ww >> 2)) * M + i) * 4 + (ww & 3)];
+            const uint32_t g0 = prow[((size_t)(ww >> 2) * M + i) * 4 + (ww & 3)];
+            const uint32_t g1 = prow[((size_t)(W4 + (ww >> 2)) * M + i) * 4 + (ww & 3)];
+            // genotype 2 by NOR, without the pad positions past the class's last sample
+            const int nv = Nc - 32 * ww;
+            const uint32_t valid = nv >= 32 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : (1u << nv) - 1u);
+            const uint32_t g2 = ~(g0 | g1) & valid;
+            // the two counted genotypes, ascending (cmp_geno)
+            const uint32_t mk0 = drop == 0 ? g1 : g0;
+            const uint32_t mk1 = drop == 2 ? g1 : g2;
             uint32_t v0[5], v1[5];
             cmp_masks(mk0, v0);
             cmp_masks(mk1, v1);
@@ -524,9 +575,11 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                 regs[q] = rR.s;
                 ring_next(rR, kCmpRegions);
             }
+            // the derived first-SNP genotype; the first SNP's inputs relabelled
+            const int dsel = __ldg(&a.firsts[T.f].drop);
             int2 mx[2];
-            mx[0] = __ldg(pt.marg + i);
-            mx[1] = __ldg(pt.marg + M + i);
+            mx[0] = relabel_marg(__ldg(pt.marg + i), pt.n_c[0], dsel);
+            mx[1] = relabel_marg(__ldg(pt.marg + M + i), pt.n_c[1], dsel);
             int cur_h = -1, j = 0;
             bool jrow = false;
             RowCells rcl[2];
@@ -550,8 +603,8 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                         my[0] = __ldg(pt.marg + j);
                         my[1] = __ldg(pt.marg + M + j);
                     }
-                    rcl[0] = row_cells(pxy[0], mx[0], my[0], pt.n_c[0]);
-                    rcl[1] = row_cells(pxy[1], mx[1], my[1], pt.n_c[1]);
+                    rcl[0] = row_cells(relabel_xy(pxy[0], my[0], dsel), mx[0], my[0], pt.n_c[0]);
+                    rcl[1] = row_cells(relabel_xy(pxy[1], my[1], dsel), mx[1], my[1], pt.n_c[1]);
                 }
                 const float thr_g = __uint_as_float(*(volatile unsigned*)&ctrl->thr);
                 // this thread's two triplets: k = kb0 + 8 H + tcol + m; pair-table rows first
@@ -570,6 +623,10 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                         tmk[m][c] = __ldg(pt.margf + (size_t)c * M + kq);
                     }
                 }
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) tik[m][c] = relabel_xz(tik[m][c], tmk[m][c], dsel);
                 uint32_t v[kCmpSets][8];
 #pragma unroll
                 for (int q = 0; q < kCmpSets; ++q)
@@ -644,6 +701,8 @@ __global__ void __launch_bounds__(kCmpThreads, 1) scan_cmp_kernel(const CmpArgs 
                         cells_u(n8[c], rcl[c], make_float4(xz[c][0][0], xz[c][0][1], xz[c][1][0], xz[c][1][1]),
                                 make_float4(yz[c][0][0], yz[c][0][1], yz[c][1][0], yz[c][1][1]),
                                 make_float2(mz[c][0], mz[c][1]), c ? u1 : u0);
+                    canon_rows(u0, dsel);
+                    canon_rows(u1, dsel);
                     int r0[kCells], r1[kCells];
                     if (!counts_of(u0, u1, pt.n_c[0], pt.n_c[1], r0, r1)) {
                         atomicOr(&ctrl->status, kStBadCount);

@@ -222,3 +222,31 @@ def test_both_kernel_forms(m, n, n1):
         with pytest.raises(epi.Epi3Error) as ei:
             h.set_option("mma_form", "wide")
         assert ei.value.code == epi.ERR_ARG
+
+
+@pytest.mark.parametrize("form", ["plain", "split"])
+def test_compacted_form_derives_each_first_snp_genotype(form):
+    # the compacted form counts the two least frequent genotypes of each first SNP and derives
+    # the third.  Here the most frequent genotype of several SNPs differs between the classes
+    # (controls mostly 0, cases mostly 1) or is genotype 2, and those SNPs dominate the top of
+    # the ranking: the pruned scan's top-k (every table cell of one class meeting the same
+    # cell of the other in the bound) must still equal the oracle's
+    rng = np.random.default_rng(77)
+    m, n, n1 = 150, 6000, 2600
+    g = rng.binomial(2, rng.uniform(0.05, 0.5, size=m)[:, None], size=(m, n)).astype(np.uint8)
+    ph = np.zeros(n, np.uint8)
+    ph[rng.choice(n, n1, replace=False)] = 1
+    case = ph == 1
+    for s in (3, 40, 41, 97):       # majority 0 in controls, 1 in cases
+        g[s, ~case] = rng.choice(3, size=(~case).sum(), p=[0.6, 0.3, 0.1])
+        g[s, case] = rng.choice(3, size=case.sum(), p=[0.25, 0.55, 0.2])
+    for s in (10, 120):             # majority 2 in both classes
+        g[s] = rng.choice(3, size=n, p=[0.15, 0.25, 0.6])
+    otr, osc, _ = oracle.scan_topk(g, ph, 24)
+    with epi.Handle(g, ph) as h:
+        h.set_option("path", "mma4c")
+        h.set_option("mma_form", form)
+        tr, sc = h.scan(24)
+        assert h.stats()["k2_prune_bound"] > 0
+    assert np.array_equal(tr, otr), (tr[:6], otr[:6])
+    assert np.array_equal(sc, osc)
