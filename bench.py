@@ -48,7 +48,11 @@ L2_FLUSH_BYTES = 512 << 20    # > 129 MB L2
 # an entry is removed whenever that kernel changes.
 TRAFFIC = {
     ("mma4", "large"): 567.59e6 + 7.07e6,   # scan_mma_kernel<e2m1> (plain form), 2048 x 16384
+    # scan_cmp_kernel (paired form), 2048 x 16384, 2 GiB ranges: DRAM read + write of one scan's
+    # seven range launches (the unit `achieved` is taken over), mean of three scans
+    ("mma4c", "large"): (27.485e9 + 27.382e9 + 26.636e9) / 3 + 9.1e6,
 }
+LG2_PER_SM_CLK = 25.2         # lg2.approx.ftz.f32 results per SM per clock (measured, microbench mufu_lg2)
 
 
 def env_int(name, default):
@@ -179,13 +183,25 @@ def roofline_of(path, m, n, world, kern_s, n_sm, peaks, config, cmp_frac=1.0):
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         peak = bf16 * 6.0
         achieved = units * cmp_frac * 8.0 / kern_s / 1e12
+        # the epilogue's own bound: the table-free K2 bound takes three lg2 per cell, 81 per
+        # triplet, on the MUFU pipe
+        lg2_peak = n_sm * sm_max * 1e6 * LG2_PER_SM_CLK
+        lg2_rate = gen.n_triplets(m) / world * 81.0 / kern_s
         return {"bound": "tensor", "kernel": "scan_cmp_kernel (e2m1)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
+                "traffic_note": "DRAM bytes of one whole scan's range launches (the unit of "
+                                "achieved); the compacted chunks it reads once are about half",
                 "peak_note": f"measured bf16 dense {bf16:.1f} TFLOP/s (burst) x 6 (e2m1/bf16 nominal ratio)",
                 "work_note": f"8 FLOP (4 useful 0/1 MACs) per sample-triplet whose first-SNP "
                              f"genotype is one of its two counted ones ({cmp_frac:.4f} of all); "
-                             f"tile waste excluded"}
+                             f"tile waste excluded",
+                "epilogue": {"bound": "mufu", "achieved": lg2_rate / 1e12, "peak": lg2_peak / 1e12,
+                             "unit": "Tlg2/s", "frac": lg2_rate / lg2_peak,
+                             "peak_note": f"{n_sm} SMs x {sm_max:.0f} MHz x {LG2_PER_SM_CLK} lg2/SM/clk "
+                                          "(measured lg2.approx throughput)",
+                             "work_note": "81 lg2 per triplet (the table-free K2 bound, three per "
+                                          "cell); the epilogue bounds this kernel"}}
     if path in (3, 4, 5):
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         ratio, elem = {3: (2.0, "e4m3"), 4: (1.0, "f16"), 5: (6.0, "e2m1")}[path]
