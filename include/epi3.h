@@ -140,11 +140,13 @@ int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* o
  * table (cell = the genotypes read as base-3 digits, x_0 most significant: 9 gX + 3 gY + gZ
  * for three) and its K2; the top_k sets by (K2 ascending, then the indices in order) are
  * returned.
- *   order        2 (= epi3_scan_pairs), 3 (= epi3_scan), or 4: every 4-SNP set counted by
- *                AND + POPC over the bit planes (81 cells, plane 2 by NOR) and scored in FP64
- *                in cell order 0..80 with the rescoring table (needs M >= 4, class sizes and
- *                M below 65536, and at most 4 GiB of selection scratch, about
- *                C(M,4) / 2048 * top_k * 32 bytes); other orders give EPI3_ERR_UNSUPPORTED.
+ *   order        2 (= epi3_scan_pairs), 3 (= epi3_scan), or 4, 5, 6: every set counted by
+ *                AND + POPC over the bit planes (81, 243 or 729 cells, plane 2 by NOR; order 4
+ *                one set per thread, orders 5 and 6 one set per warp) and scored in FP64 in
+ *                cell order with the rescoring table (needs M >= order, class sizes and M
+ *                below 65536, and at most 4 GiB of selection scratch, about
+ *                C(M, order) / 2048 * top_k * 32 bytes); other orders give
+ *                EPI3_ERR_UNSUPPORTED.
  *   top_k        1..min(EPI3_MAX_TOPK, C(M, order)).
  *   out_snps     [top_k][order] int32, increasing within a row, 0-based.
  *   out_scores   [top_k] FP64 K2, ascending.

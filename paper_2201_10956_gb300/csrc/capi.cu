@@ -1174,38 +1174,44 @@ int epi3_scan_order(epi3_handle* h, int32_t order, int32_t top_k, int32_t* out_s
     g_err.clear();
     (void)cudaGetLastError();  // do not report an earlier call's error as ours
     if (!h) return fail(EPI3_ERR_ARG, "null handle");
-    if (order != 4) return fail(EPI3_ERR_UNSUPPORTED, "interaction order %d (2, 3 and 4 are built)", order);
+    if (order < 2 || order > 6)
+        return fail(EPI3_ERR_UNSUPPORTED, "interaction order %d (2 to 6 are built)", order);
     if (!out_snps || !out_scores) return fail(EPI3_ERR_ARG, "null output pointer");
-    if (h->M < 4) return fail(EPI3_ERR_ARG, "order 4 needs at least 4 SNPs");
-    const long long nq = quad_count(h->M);
+    if (h->M < order) return fail(EPI3_ERR_ARG, "order %d needs at least %d SNPs", order, order);
+    const long long nq = order_count(h->M, order);
     if (top_k < 1 || top_k > EPI3_MAX_TOPK || top_k > nq)
         return fail(EPI3_ERR_ARG, "top_k %d outside 1..min(%d, %lld)", top_k, EPI3_MAX_TOPK, nq);
     if (h->N0 >= 65536 || h->N1 >= 65536 || h->M >= 65536)
-        return fail(EPI3_ERR_UNSUPPORTED, "the four-SNP scan needs class sizes and n_snps below 65536");
-    const size_t sel = (quad_scan_scratch(h->M, top_k) + 255) & ~(size_t)255;
+        return fail(EPI3_ERR_UNSUPPORTED, "the %d-SNP scan needs class sizes and n_snps below 65536", order);
+    const size_t sel = ((order == 4 ? quad_scan_scratch(h->M, top_k)
+                                    : order_scan_scratch(h->M, order, top_k)) + 255) & ~(size_t)255;
     if (sel > (size_t)4 << 30)
-        return fail(EPI3_ERR_UNSUPPORTED, "four-SNP scan of %d SNPs with top_k %d needs %zu bytes of "
-                    "selection scratch (limit 4 GiB)", h->M, top_k, sel);
-    const size_t need = sel + sizeof(double) * (size_t)top_k + sizeof(int32_t) * 4 * (size_t)top_k;
+        return fail(EPI3_ERR_UNSUPPORTED, "%d-SNP scan of %d SNPs with top_k %d needs %zu bytes of "
+                    "selection scratch (limit 4 GiB)", order, h->M, top_k, sel);
+    const size_t need = sel + sizeof(double) * (size_t)top_k + sizeof(int32_t) * order * (size_t)top_k;
     if (h->pair_scratch_bytes < need) {
         cudaFree(h->d_pair_scratch);
         h->d_pair_scratch = nullptr;
         h->pair_scratch_bytes = 0;
-        CK(dev_alloc(&h->d_pair_scratch, need), "alloc four-SNP scan scratch");
+        CK(dev_alloc(&h->d_pair_scratch, need), "alloc k-SNP scan scratch");
         h->pair_scratch_bytes = need;
     }
     double* d_s = reinterpret_cast<double*>(static_cast<char*>(h->d_pair_scratch) + sel);
     int32_t* d_sets = reinterpret_cast<int32_t*>(d_s + top_k);
     CK(cudaEventRecord(h->ev[0], h->stream), "event");
-    CK(launch_quad_scan(h->pl, h->k2.lf64, h->N0, h->N1, top_k, h->d_pair_scratch, d_sets, d_s,
-                        h->stream), "four-SNP scan launch");
+    if (order == 4)
+        CK(launch_quad_scan(h->pl, h->k2.lf64, h->N0, h->N1, top_k, h->d_pair_scratch, d_sets, d_s,
+                            h->stream), "four-SNP scan launch");
+    else
+        CK(launch_order_scan(h->pl, h->k2.lf64, order, top_k, h->d_pair_scratch, d_sets, d_s, h->stream),
+           "k-SNP scan launch");
     CK(cudaEventRecord(h->ev[1], h->stream), "event");
     const cudaMemcpyKind kind =
         (h->flags & EPI3_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    CK(cudaMemcpyAsync(out_snps, d_sets, sizeof(int32_t) * 4 * top_k, kind, h->stream),
+    CK(cudaMemcpyAsync(out_snps, d_sets, sizeof(int32_t) * order * top_k, kind, h->stream),
        "copy sets");
     CK(cudaMemcpyAsync(out_scores, d_s, sizeof(double) * top_k, kind, h->stream), "copy scores");
-    CK(cudaStreamSynchronize(h->stream), "four-SNP scan");
+    CK(cudaStreamSynchronize(h->stream), "k-SNP scan");
     epi3_stats& s = h->stats;
     s.n_triplets = nq;  // sets scored
     s.n_candidates = 0;

@@ -127,6 +127,11 @@ cudaError_t launch_pair_scan(const PairTables& pt, const double* lf64, int M, in
                              void* scratch, int32_t* out_pairs, double* out_s, cudaStream_t st);
 // Four-SNP scan (Eq. 1 for four SNPs, 81 cells): the k best sets by (FP64 K2, i, j, k, l) from
 // the bit planes; needs both class sizes below 65536 and M below 65536.
+// orders 5 and 6: every set by AND + POPC (one warp per set), FP64 K2 in cell order
+long long order_count(int M, int order);
+size_t order_scan_scratch(int M, int order, int k);
+cudaError_t launch_order_scan(const Planes& pl, const double* lf64, int order, int k, void* scratch,
+                              int32_t* out_snps, double* out_s, cudaStream_t st);
 long long quad_count(int M);
 size_t quad_scan_scratch(int M, int k);
 cudaError_t launch_quad_scan(const Planes& pl, const double* lf64, int n0, int n1, int k,

@@ -1,4 +1,4 @@
-// Scans of other interaction orders: Eq. 1 applied to two SNPs and to four SNPs.
+// Scans of other interaction orders: Eq. 1 applied to two, four, five and six SNPs.
 //
 // Pairs: every pair i < j gets the 3^2-cell x {control, case} table and its FP64 K2; the k
 // lowest are returned in the total order (K2 ascending, then i, j).  The counts are exact
@@ -260,7 +260,185 @@ __global__ void quad_emit_kernel(const Item* __restrict__ best, int k, int32_t* 
     }
 }
 
+// ---------------------------------------------------------------- five and six SNPs
+// The same table and score for order K = 5, 6 (3^K = 243, 729 cells), one warp per set: lane l
+// owns cells l, l + 32, ..., each cell's genotype digits kept as 2-bit codes (x_0 most
+// significant, as in the cell index); per 32-sample word every lane ANDs the K plane words its
+// cells select and adds the POPC (both classes packed in one counter, class 1 in the high
+// half).  The FP64 K2 is then summed in cell order 0 .. 3^K - 1 by every lane from the lanes'
+// terms (warp shuffles in cell order), as the oracle adds them.  Sets are enumerated in
+// lexicographic order, so the rank q itself is the tie key.
+constexpr int kOrdThreads = 256;      // 8 warps per block, 256 sets each
+
+template <int K>
+struct Pow3 {
+    static constexpr int v = 3 * Pow3<K - 1>::v;
+};
+template <>
+struct Pow3<0> {
+    static constexpr int v = 1;
+};
+
+// The q-th K-set x_0 < ... < x_{K-1} of M SNPs in lexicographic order.
+template <int K>
+__device__ inline void decode_lex(long long q, int M, int* x) {
+    int v = 0;
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        for (;; ++v) {
+            const long long c = choose_ll(M - 1 - v, K - 1 - t);   // sets with x_t = v
+            if (q < c) {
+                x[t] = v++;
+                break;
+            }
+            q -= c;
+        }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kOrdThreads)
+order_score_kernel(Planes pl, const double* __restrict__ lf64, long long n_sets, int k,
+                   Item* __restrict__ out) {
+    constexpr int kCellsK = Pow3<K>::v, kPer = (kCellsK + 31) / 32;
+    __shared__ Item it[kPairBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int M = pl.M;
+    uint32_t code[kPer];   // 2 bits per SNP: the genotype of x_t at bits 2 t
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) {
+        int e = lane + 32 * m < kCellsK ? lane + 32 * m : 0;
+        uint32_t cd = 0u;
+#pragma unroll
+        for (int t = K - 1; t >= 0; --t) {
+            cd |= (uint32_t)(e % 3) << (2 * t);
+            e /= 3;
+        }
+        code[m] = cd;
+    }
+    const long long q0 = (long long)blockIdx.x * kPairBlock;
+    for (int t = warp; t < kPairBlock; t += kOrdThreads / 32) {
+        const long long q = q0 + t;
+        if (q >= n_sets) {   // uniform over the warp
+            if (lane == 0) it[t] = pad_item();
+            continue;
+        }
+        int x[K];
+        decode_lex<K>(q, M, x);
+        uint32_t cnt[kPer];
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) cnt[m] = 0u;
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            const long long coff = c ? pl.coff[1] : pl.coff[0];
+            const int W4 = c ? pl.W4[1] : pl.W4[0];
+            const int sh = 16 * c;
+#pragma unroll 1
+            for (int w4 = 0; w4 < W4; ++w4) {
+                uint4 g0[K], g1[K];
+#pragma unroll
+                for (int v = 0; v < K; ++v) {
+                    g0[v] = __ldg(pl.planes + coff + (size_t)w4 * M + x[v]);
+                    g1[v] = __ldg(pl.planes + coff + (size_t)(W4 + w4) * M + x[v]);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t P[K][3];
+#pragma unroll
+                    for (int v = 0; v < K; ++v) {
+                        const uint32_t a0 = e == 0 ? g0[v].x : e == 1 ? g0[v].y : e == 2 ? g0[v].z : g0[v].w;
+                        const uint32_t a1 = e == 0 ? g1[v].x : e == 1 ? g1[v].y : e == 2 ? g1[v].z : g1[v].w;
+                        P[v][0] = a0;
+                        P[v][1] = a1;
+                        P[v][2] = ~(a0 | a1);        // genotype 2, Sec. IV-A (pad bits read 2)
+                    }
+#pragma unroll
+                    for (int m = 0; m < kPer; ++m) {
+                        uint32_t acc = 0xFFFFFFFFu;
+#pragma unroll
+                        for (int v = 0; v < K; ++v) {
+                            const uint32_t g = (code[m] >> (2 * v)) & 3u;
+                            acc &= g == 0u ? P[v][0] : (g == 1u ? P[v][1] : P[v][2]);
+                        }
+                        cnt[m] += (uint32_t)__popc(acc) << sh;
+                    }
+                }
+            }
+        }
+        // pad samples read genotype 2 in every SNP: the last cell only
+        if (lane == (kCellsK - 1) % 32)
+            cnt[(kCellsK - 1) / 32] -= (uint32_t)pl.pad[0] + ((uint32_t)pl.pad[1] << 16);
+        double term[kPer];
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+            const int r0 = (int)(cnt[m] & 0xFFFFu), r1 = (int)(cnt[m] >> 16);
+            term[m] = lane + 32 * m < kCellsK
+                          ? __dsub_rn(__dsub_rn(lf64[r0 + r1 + 1], lf64[r0]), lf64[r1]) : 0.0;
+        }
+        double sc = 0.0;
+#pragma unroll
+        for (int m = 0; m < kPer; ++m)
+#pragma unroll
+            for (int l = 0; l < 32; ++l)
+                if (32 * m + l < kCellsK) sc = __dadd_rn(sc, __shfl_sync(0xffffffffu, term[m], l));
+        if (lane == 0) it[t] = Item{sc, q};
+    }
+    __syncthreads();
+    sort_items(it);
+    for (int t = threadIdx.x; t < k; t += kOrdThreads) out[(long long)blockIdx.x * k + t] = it[t];
+}
+
+template <int K>
+__global__ void order_emit_kernel(const Item* __restrict__ best, int k, int M,
+                                  int32_t* __restrict__ out_snps, double* __restrict__ out_s) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        const Item e = best[t];
+        int x[K];
+        decode_lex<K>(e.key, M, x);
+#pragma unroll
+        for (int v = 0; v < K; ++v) out_snps[K * t + v] = (int32_t)x[v];
+        out_s[t] = e.s;
+    }
+}
+
+template <int K>
+cudaError_t order_scan_k(const Planes& pl, const double* lf64, int k, void* scratch,
+                         int32_t* out_snps, double* out_s, cudaStream_t st) {
+    const long long n_sets = choose_ll(pl.M, K);
+    long long blocks = (n_sets + kPairBlock - 1) / kPairBlock;
+    Item* a = static_cast<Item*>(scratch);
+    Item* b = a + blocks * k;
+    order_score_kernel<K><<<(unsigned)blocks, kOrdThreads, 0, st>>>(pl, lf64, n_sets, k, a);
+    cudaError_t e = cudaGetLastError();
+    long long n = blocks * k;
+    while (e == cudaSuccess && blocks > 1) {
+        blocks = (n + kPairBlock - 1) / kPairBlock;
+        pair_merge_kernel<<<(unsigned)blocks, kPairThreads, 0, st>>>(a, n, k, b);
+        e = cudaGetLastError();
+        n = blocks * k;
+        Item* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    if (e != cudaSuccess) return e;
+    order_emit_kernel<K><<<1, 512, 0, st>>>(a, k, pl.M, out_snps, out_s);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+long long order_count(int M, int order) { return choose_ll(M, order); }
+
+size_t order_scan_scratch(int M, int order, int k) {
+    const long long blocks = (choose_ll(M, order) + kPairBlock - 1) / kPairBlock;
+    return (size_t)2 * (size_t)blocks * (size_t)k * sizeof(Item);
+}
+
+cudaError_t launch_order_scan(const Planes& pl, const double* lf64, int order, int k, void* scratch,
+                              int32_t* out_snps, double* out_s, cudaStream_t st) {
+    if (order == 5) return order_scan_k<5>(pl, lf64, k, scratch, out_snps, out_s, st);
+    if (order == 6) return order_scan_k<6>(pl, lf64, k, scratch, out_snps, out_s, st);
+    return cudaErrorInvalidValue;
+}
 
 long long quad_count(int M) { return choose_ll(M, 4); }
 

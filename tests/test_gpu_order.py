@@ -1,8 +1,9 @@
-"""Interaction orders beyond three (needs an sm_103 GPU): epi3_scan_order at order 4 (Eq. 1 for
-four SNPs, 81 cells per class) against the CPU oracle's generic-order scan -- identical SNP
-sets and bit-identical FP64 scores -- on tiny inputs with ragged class sizes, one class only,
-exact ties from a duplicated SNP column, and the minimum of four SNPs; orders 2 and 3 route to
-the pairwise and triplet scans."""
+"""Interaction orders beyond three (needs an sm_103 GPU): epi3_scan_order at orders 4, 5 and 6
+(Eq. 1 for four, five and six SNPs: 81, 243 and 729 cells per class) against the CPU oracle's
+generic-order scan -- identical SNP sets and bit-identical FP64 scores -- on tiny inputs with
+ragged class sizes, one class only, exact ties from a duplicated SNP column, and the minimum
+number of SNPs; orders 2 and 3 route to the pairwise and triplet scans, other orders are
+refused."""
 import numpy as np
 import pytest
 
@@ -49,9 +50,38 @@ def test_orders_2_and_3_route_to_the_pair_and_triplet_scans():
         p2, s2 = h.scan_order(2, 20)
         p3, s3 = h.scan_order(3, 20)
         with pytest.raises(epi.Epi3Error) as ei:
-            h.scan_order(5, 3)
+            h.scan_order(7, 3)
+        assert ei.value.code == epi.ERR_UNSUPPORTED
+        with pytest.raises(epi.Epi3Error) as ei:
+            h.scan_order(1, 3)
         assert ei.value.code == epi.ERR_UNSUPPORTED
     o2, os2, _ = oracle.scan_order_topk(g, ph, 2, 20)
     o3, os3, _ = oracle.scan_order_topk(g, ph, 3, 20)
     assert np.array_equal(p2, o2) and np.array_equal(s2, os2)
     assert np.array_equal(p3, o3) and np.array_equal(s3, os3)
+
+
+@pytest.mark.parametrize("order,m,n,n1,k", [(5, 5, 40, 17, 1), (5, 16, 300, 133, 40),
+                                            (5, 22, 257, 0, 25), (5, 20, 1000, 999, 100),
+                                            (6, 6, 90, 44, 1), (6, 14, 129, 64, 64),
+                                            (6, 17, 700, 300, 512)])
+def test_orders_5_and_6_match_oracle(order, m, n, n1, k):
+    g, ph = pins.tiny_data(m, n, n1, seed=730 + 10 * order + m)
+    with epi.Handle(g, ph) as h:
+        sets, sc = h.scan_order(order, k)
+    osets, osc, _ = oracle.scan_order_topk(g, ph, order, k)
+    assert np.array_equal(sets, osets), (sets[:3], osets[:3])
+    assert np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("order", [5, 6])
+def test_orders_5_and_6_exact_ties(order):
+    g, ph = pins.tiny_data(15, 600, 280, seed=740 + order)
+    g[14] = g[13]                           # sets ending in 13 or 14 tie exactly
+    with epi.Handle(g, ph) as h:
+        sets, sc = h.scan_order(order, 150)
+        with pytest.raises(epi.Epi3Error) as ei:
+            h.scan_order(order, 4000)       # above EPI3_MAX_TOPK
+        assert ei.value.code == epi.ERR_ARG
+    osets, osc, _ = oracle.scan_order_topk(g, ph, order, 150)
+    assert np.array_equal(sets, osets) and np.array_equal(sc, osc)
