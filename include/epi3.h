@@ -156,7 +156,15 @@ int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* o
 int epi3_scan_order(epi3_handle* h, int32_t order, int32_t top_k, int32_t* out_snps,
                     double* out_scores);
 
-/* Release the handle's device memory, stream (if owned) and events. */
+/*
+ * Release the handle's device memory, stream (if owned) and events.  Device memory of handles
+ * and batches goes to a per-process cache instead of back to the driver (the device is
+ * synchronised first, as cudaFree would do), and later handles take their buffers from it:
+ * creating and destroying a handle per data set then costs no cudaMalloc / cudaFree.  The
+ * environment variable EPI3_CACHE_MB (read once) bounds the cache, default 4096 MB per
+ * process, oldest blocks released first; 0 turns it off.  An allocation that fails while
+ * blocks are cached empties the cache and tries again.
+ */
 int epi3_destroy(epi3_handle* h);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <string>
 #include <chrono>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "epi3_internal.cuh"
@@ -51,11 +53,118 @@ bool inject(const char* what) {
     return f && strcmp(f, what) == 0;
 }
 
+// Device memory of handles and batches.  Freed blocks are kept in a per-process cache (per
+// device, at most EPI3_CACHE_MB megabytes, default 4096; 0 turns the cache off) and handed to
+// later allocations of up to their size, so that creating and destroying handles per data set
+// does not pay cudaMalloc and cudaFree each time.  A block enters the cache only after its
+// device is synchronised, as cudaFree would do, so no queued kernel can still use it.  An
+// allocation that fails while blocks are cached empties the cache and tries once more.
+struct MemBlock {
+    void* p;
+    size_t bytes;
+    int dev;
+};
+std::mutex g_mem_mu;
+std::unordered_map<void*, MemBlock> g_mem_live;   // blocks handed out by dev_alloc
+std::vector<MemBlock> g_mem_free;                 // cached blocks
+size_t g_mem_free_bytes = 0;
+
+size_t mem_cache_limit() {
+    static const size_t lim = [] {
+        const char* v = getenv("EPI3_CACHE_MB");
+        long long mb = v ? atoll(v) : 4096;
+        return (size_t)(mb < 0 ? 0 : mb) << 20;
+    }();
+    return lim;
+}
+
+void mem_drop_cache() {  // caller holds g_mem_mu
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (const MemBlock& b : g_mem_free) {
+        if (b.dev != cur) cudaSetDevice(b.dev);
+        cudaFree(b.p);
+        if (b.dev != cur) cudaSetDevice(cur);
+    }
+    g_mem_free.clear();
+    g_mem_free_bytes = 0;
+}
+
 cudaError_t dev_alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (inject("alloc")) return cudaErrorMemoryAllocation;
-    if (bytes == 0) bytes = 16;
-    return cudaMalloc(p, bytes);
+    bytes = (std::max(bytes, (size_t)16) + 255) & ~(size_t)255;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    // the smallest cached block of this device that holds the request without wasting more
+    // than the request itself
+    size_t best = (size_t)-1;
+    for (size_t t = 0; t < g_mem_free.size(); ++t) {
+        const MemBlock& b = g_mem_free[t];
+        if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes &&
+            (best == (size_t)-1 || b.bytes < g_mem_free[best].bytes))
+            best = t;
+    }
+    if (best != (size_t)-1) {
+        const MemBlock b = g_mem_free[best];
+        g_mem_free[best] = g_mem_free.back();
+        g_mem_free.pop_back();
+        g_mem_free_bytes -= b.bytes;
+        g_mem_live[b.p] = b;
+        *p = b.p;
+        return cudaSuccess;
+    }
+    e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation && !g_mem_free.empty()) {
+        (void)cudaGetLastError();
+        mem_drop_cache();
+        e = cudaMalloc(p, bytes);
+    }
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    g_mem_live[*p] = MemBlock{*p, bytes, dev};
+    return cudaSuccess;
+}
+
+// Release a block of dev_alloc (null is ignored; anything else goes to cudaFree).
+void dev_free(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    const auto it = g_mem_live.find(p);
+    if (it == g_mem_live.end()) {
+        cudaFree(p);
+        return;
+    }
+    const MemBlock b = it->second;
+    g_mem_live.erase(it);
+    const size_t lim = mem_cache_limit();
+    if (b.bytes > lim) {
+        cudaFree(p);
+        return;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (b.dev != cur) cudaSetDevice(b.dev);
+    const cudaError_t e = cudaDeviceSynchronize();   // as cudaFree: no queued work still uses it
+    if (b.dev != cur) cudaSetDevice(cur);
+    if (e != cudaSuccess) {   // a failed context: give the block back to the driver
+        cudaFree(p);
+        return;
+    }
+    while (g_mem_free_bytes + b.bytes > lim && !g_mem_free.empty()) {   // oldest first
+        const MemBlock o = g_mem_free.front();
+        g_mem_free.erase(g_mem_free.begin());
+        g_mem_free_bytes -= o.bytes;
+        if (o.dev != cur) cudaSetDevice(o.dev);
+        cudaFree(o.p);
+        if (o.dev != cur) cudaSetDevice(cur);
+    }
+    g_mem_free.push_back(b);
+    g_mem_free_bytes += b.bytes;
 }
 
 long long pairs(long long m) { return m < 2 ? 0 : m * (m - 1) / 2; }
@@ -142,25 +251,25 @@ namespace {
 void release(epi3_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    cudaFree(h->d_planes);
-    cudaFree(h->d_lf2);
-    cudaFree(h->d_lf64);
-    cudaFree(h->d_ctrl);
-    cudaFree(h->d_cand);
-    cudaFree(h->d_fin);
-    cudaFree(h->d_out_scores);
-    cudaFree(h->d_out_trip);
-    cudaFree(h->d_pt);
-    cudaFree(h->d_pair_scratch);
-    cudaFree(h->d_marg);
-    cudaFree(h->d_ptf);
-    cudaFree(h->d_margf);
-    cudaFree(h->d_oh);
-    cudaFree(h->d_cmp);
-    cudaFree(h->d_firsts);
-    cudaFree(h->d_tiles);
-    cudaFree(h->d_cd);
-    cudaFree(h->d_prof);
+    dev_free(h->d_planes);
+    dev_free(h->d_lf2);
+    dev_free(h->d_lf64);
+    dev_free(h->d_ctrl);
+    dev_free(h->d_cand);
+    dev_free(h->d_fin);
+    dev_free(h->d_out_scores);
+    dev_free(h->d_out_trip);
+    dev_free(h->d_pt);
+    dev_free(h->d_pair_scratch);
+    dev_free(h->d_marg);
+    dev_free(h->d_ptf);
+    dev_free(h->d_margf);
+    dev_free(h->d_oh);
+    dev_free(h->d_cmp);
+    dev_free(h->d_firsts);
+    dev_free(h->d_tiles);
+    dev_free(h->d_cd);
+    dev_free(h->d_prof);
     cudaFreeHost(h->h_ctrl);
     cudaFreeHost(h->h_scores);
     cudaFreeHost(h->h_trip);
@@ -234,7 +343,7 @@ int build_k2_tables(epi3_handle* h) {
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(&delta, d_err, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-    cudaFree(d_err);
+    dev_free(d_err);
     CK(ce, "approx error");
     const double u = std::ldexp(1.0, -24), ln2 = std::log(2.0);
     const double kmax = 27.0 * std::log((double)h->N + 2.0) + (double)h->N * ln2;
@@ -260,10 +369,10 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     int rc = EPI3_OK;
     auto cleanup = [&]() {
         if (!(h->flags & EPI3_DEVICE_PTRS)) {
-            cudaFree(d_geno);
-            cudaFree(d_pheno);
+            dev_free(d_geno);
+            dev_free(d_pheno);
         }
-        cudaFree(d_counts);
+        dev_free(d_counts);
     };
     do {
         cudaError_t e;
@@ -358,7 +467,7 @@ int ensure_onehot(epi3_handle* h, int kind) {
     const int rc = ensure_pair_floats(h);
     if (rc != EPI3_OK) return rc;
     if (h->d_oh && h->oh_kind == kind) return EPI3_OK;
-    cudaFree(h->d_oh);
+    dev_free(h->d_oh);
     h->d_oh = nullptr;
     const int spk = mma_samples_per_step(kind);
     // N_c samples plus the bias sample (position N_c) of a non-empty class
@@ -429,14 +538,14 @@ int whole_scan_tiles(epi3_handle* h) {
         if (e == cudaSuccess) e = launch_tile_list(d_blocks, (int)blocks.size(), 0, h->d_tiles, h->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d_blocks);
+    dev_free(d_blocks);
     CK(e, "tile list");
     return EPI3_OK;
 }
 
 int ensure_tiles(epi3_handle* h, long long pb, long long pe) {
     if (h->d_tiles && h->tiles_pb == pb && h->tiles_pe == pe) return EPI3_OK;
-    cudaFree(h->d_tiles);
+    dev_free(h->d_tiles);
     h->d_tiles = nullptr;
     // whole scan: every pair with a third SNP after it (scan_impl clamps the range to these)
     // (offsets fit int: the tile list is capped)
@@ -500,7 +609,7 @@ int finish_scan(epi3_handle* h, int top_k, int attempt) {
     if (st & kStCandOverflow) {
         if (h->cand_cap >= (1LL << 24) || attempt >= 3)
             return fail(EPI3_ERR_OVERFLOW, "more than %lld FP32 candidates", h->cand_cap);
-        cudaFree(h->d_cand);
+        dev_free(h->d_cand);
         h->d_cand = nullptr;
         h->cand_cap *= 8;
         CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
@@ -740,7 +849,7 @@ int cmp_prepare(epi3_handle* h, long long pb, long long pe, CmpPlan& P) {
                       cudaMemcpyDeviceToHost), "read marginals");
     }
     plan_cmp(h, pb, pe, P);
-    cudaFree(h->d_firsts);
+    dev_free(h->d_firsts);
     h->d_firsts = nullptr;
     if (!P.firsts.empty()) {
         CK(dev_alloc((void**)&h->d_firsts, sizeof(CmpFirst) * P.firsts.size()), "alloc first-SNP table");
@@ -763,7 +872,7 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
     h->last_cmp_chunks = P.chunks_total;
     h->last_cmp_steps = P.steps_total;
     if (h->cmp_bytes < need) {
-        cudaFree(h->d_cmp);
+        dev_free(h->d_cmp);
         h->d_cmp = nullptr;
         h->cmp_bytes = 0;
         CK(dev_alloc((void**)&h->d_cmp, need), "alloc compacted chunks");
@@ -952,7 +1061,7 @@ int scan_impl(epi3_handle* h, long long pb, long long pe, int top_k, int32_t* ou
         if (st & kStCandOverflow) {
             if (h->cand_cap >= (1LL << 24) || attempt >= 3)
                 return fail(EPI3_ERR_OVERFLOW, "more than %lld FP32 candidates", h->cand_cap);
-            cudaFree(h->d_cand);
+            dev_free(h->d_cand);
             h->d_cand = nullptr;
             h->cand_cap *= 8;
             CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
@@ -1040,10 +1149,10 @@ int per_triplet(epi3_handle* h, long long n, const int32_t* trip, int32_t* out_c
         if (h->h_ctrl->status & kStBadIndex) rc = fail(EPI3_ERR_ARG, "triplet index outside 0..%d", h->M - 1);
     } while (0);
     if (!dev) {
-        cudaFree(d_trip);
-        cudaFree(d_counts);
-        cudaFree(d_s32);
-        cudaFree(d_s64);
+        dev_free(d_trip);
+        dev_free(d_counts);
+        dev_free(d_s32);
+        dev_free(d_s64);
     }
     return rc;
 }
@@ -1137,7 +1246,7 @@ int epi3_scan_pairs(epi3_handle* h, int32_t top_k, int32_t* out_pairs, double* o
     const size_t sel = (pair_scan_scratch(np, top_k) + 255) & ~(size_t)255;
     const size_t need = sel + sizeof(double) * (size_t)top_k + sizeof(int32_t) * 2 * (size_t)top_k;
     if (h->pair_scratch_bytes < need) {
-        cudaFree(h->d_pair_scratch);
+        dev_free(h->d_pair_scratch);
         h->d_pair_scratch = nullptr;
         h->pair_scratch_bytes = 0;
         CK(dev_alloc(&h->d_pair_scratch, need), "alloc pair-scan scratch");
@@ -1190,7 +1299,7 @@ int epi3_scan_order(epi3_handle* h, int32_t order, int32_t top_k, int32_t* out_s
                     "selection scratch (limit 4 GiB)", order, h->M, top_k, sel);
     const size_t need = sel + sizeof(double) * (size_t)top_k + sizeof(int32_t) * order * (size_t)top_k;
     if (h->pair_scratch_bytes < need) {
-        cudaFree(h->d_pair_scratch);
+        dev_free(h->d_pair_scratch);
         h->d_pair_scratch = nullptr;
         h->pair_scratch_bytes = 0;
         CK(dev_alloc(&h->d_pair_scratch, need), "alloc k-SNP scan scratch");
@@ -1272,7 +1381,7 @@ int epi3_scan_scores(epi3_handle* h, int32_t path, float* out_scores) {
         e = cudaMemcpy(out_scores, buf, n * sizeof(float), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = cuda_fail(e, "read score cube");
     }
-    if (!dev) cudaFree(buf);
+    if (!dev) dev_free(buf);
     return rc;
 }
 
@@ -1299,7 +1408,7 @@ int epi3_scan_checksum(epi3_handle* h, int32_t path, uint64_t* out_sum, int64_t*
         e = cudaMemcpy(slots, d, sizeof(slots), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = cuda_fail(e, "read checksum slots");
     }
-    cudaFree(d);
+    dev_free(d);
     if (rc != EPI3_OK) return rc;
     unsigned long long sum = 0, cnt = 0;
     for (int q = 0; q < kTsumSlots; ++q) {
@@ -1360,7 +1469,7 @@ int epi3_set_option(epi3_handle* h, const char* key, const char* value) {
     if (!strcmp(key, "candidates")) {
         const long long n = atoll(value);
         if (n < 64 || n > (1LL << 28)) return fail(EPI3_ERR_ARG, "candidates %s outside 64..2^28", value);
-        cudaFree(h->d_cand);
+        dev_free(h->d_cand);
         h->d_cand = nullptr;
         h->cand_cap = n;
         CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "alloc candidates");
@@ -1445,13 +1554,13 @@ void batch_release(epi3_batch* b) {
         h->d_ctrl = nullptr;  // owned by the batch
         release(h);
     }
-    cudaFree(b->d_ctrls);
+    dev_free(b->d_ctrls);
     cudaFreeHost(b->h_ctrls);
-    cudaFree(b->d_cds);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_cmp);
-    cudaFree(b->d_scores);
-    cudaFree(b->d_trip);
+    dev_free(b->d_cds);
+    dev_free(b->d_tiles);
+    dev_free(b->d_cmp);
+    dev_free(b->d_scores);
+    dev_free(b->d_trip);
     cudaFreeHost(b->h_scores);
     cudaFreeHost(b->h_trip);
     for (auto& e : b->ev)
@@ -1847,7 +1956,7 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
             return bail(rc);
         }
         epi3_handle* h = b->h[c];
-        cudaFree(h->d_ctrl);              // the batch keeps every control block together
+        dev_free(h->d_ctrl);              // the batch keeps every control block together
         h->d_ctrl = b->d_ctrls + c;
         if ((rc = ensure_pair_tables(h)) != EPI3_OK) return bail(rc);
     }
@@ -1956,7 +2065,7 @@ int epi3_batch_scan(epi3_batch* b, int32_t top_k, int32_t* out_triplets, double*
                 if (h->cand_cap >= (1LL << 24) || attempt >= 3)
                     return fail(EPI3_ERR_OVERFLOW, "cohort %d: more than %lld FP32 candidates", c,
                                 h->cand_cap);
-                cudaFree(h->d_cand);
+                dev_free(h->d_cand);
                 h->d_cand = nullptr;
                 h->cand_cap *= 8;
                 CK(dev_alloc((void**)&h->d_cand, sizeof(Cand) * h->cand_cap), "grow candidates");
