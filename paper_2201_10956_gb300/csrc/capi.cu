@@ -130,8 +130,10 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
     return cudaSuccess;
 }
 
-// Release a block of dev_alloc (null is ignored; anything else goes to cudaFree).
-void dev_free(void* p) {
+// Release a block of dev_alloc (null is ignored; anything else goes to cudaFree).  `synced`:
+// the caller has synchronised the only stream that used the block, so the device-wide
+// synchronisation is skipped.
+void dev_free(void* p, bool synced = false) {
     if (!p) return;
     std::lock_guard<std::mutex> lk(g_mem_mu);
     const auto it = g_mem_live.find(p);
@@ -149,7 +151,8 @@ void dev_free(void* p) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (b.dev != cur) cudaSetDevice(b.dev);
-    const cudaError_t e = cudaDeviceSynchronize();   // as cudaFree: no queued work still uses it
+    // as cudaFree: no queued work still uses the block
+    const cudaError_t e = synced ? cudaSuccess : cudaDeviceSynchronize();
     if (b.dev != cur) cudaSetDevice(cur);
     if (e != cudaSuccess) {   // a failed context: give the block back to the driver
         cudaFree(p);
@@ -165,6 +168,46 @@ void dev_free(void* p) {
     }
     g_mem_free.push_back(b);
     g_mem_free_bytes += b.bytes;
+}
+
+// Pinned host buffers of handles and batches (status and result read-back), cached the same
+// way: freed only after the stream that copied into them was synchronised.
+std::unordered_map<void*, size_t> g_pin_live;
+std::vector<std::pair<void*, size_t>> g_pin_free;
+constexpr size_t kPinCacheMax = 256;   // cached blocks
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    bytes = (std::max(bytes, (size_t)16) + 255) & ~(size_t)255;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    for (size_t t = 0; t < g_pin_free.size(); ++t)
+        if (g_pin_free[t].second >= bytes && g_pin_free[t].second <= 2 * bytes) {
+            *p = g_pin_free[t].first;
+            g_pin_live[*p] = g_pin_free[t].second;
+            g_pin_free[t] = g_pin_free.back();
+            g_pin_free.pop_back();
+            return cudaSuccess;
+        }
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    g_pin_live[*p] = bytes;
+    return cudaSuccess;
+}
+
+void host_free(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    const auto it = g_pin_live.find(p);
+    if (it == g_pin_live.end() || mem_cache_limit() == 0 || g_pin_free.size() >= kPinCacheMax) {
+        if (it != g_pin_live.end()) g_pin_live.erase(it);
+        cudaFreeHost(p);
+        return;
+    }
+    g_pin_free.emplace_back(p, it->second);
+    g_pin_live.erase(it);
 }
 
 long long pairs(long long m) { return m < 2 ? 0 : m * (m - 1) / 2; }
@@ -250,29 +293,31 @@ namespace {
 
 void release(epi3_handle* h) {
     if (!h) return;
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    dev_free(h->d_planes);
-    dev_free(h->d_lf2);
-    dev_free(h->d_lf64);
-    dev_free(h->d_ctrl);
-    dev_free(h->d_cand);
-    dev_free(h->d_fin);
-    dev_free(h->d_out_scores);
-    dev_free(h->d_out_trip);
-    dev_free(h->d_pt);
-    dev_free(h->d_pair_scratch);
-    dev_free(h->d_marg);
-    dev_free(h->d_ptf);
-    dev_free(h->d_margf);
-    dev_free(h->d_oh);
-    dev_free(h->d_cmp);
-    dev_free(h->d_firsts);
-    dev_free(h->d_tiles);
-    dev_free(h->d_cd);
-    dev_free(h->d_prof);
-    cudaFreeHost(h->h_ctrl);
-    cudaFreeHost(h->h_scores);
-    cudaFreeHost(h->h_trip);
+    // every buffer of the handle is used on its stream only: once that is synchronised
+    // the blocks go to the cache without a device-wide synchronisation
+    const bool synced = h->stream && cudaStreamSynchronize(h->stream) == cudaSuccess;
+    dev_free(h->d_planes, synced);
+    dev_free(h->d_lf2, synced);
+    dev_free(h->d_lf64, synced);
+    dev_free(h->d_ctrl, synced);
+    dev_free(h->d_cand, synced);
+    dev_free(h->d_fin, synced);
+    dev_free(h->d_out_scores, synced);
+    dev_free(h->d_out_trip, synced);
+    dev_free(h->d_pt, synced);
+    dev_free(h->d_pair_scratch, synced);
+    dev_free(h->d_marg, synced);
+    dev_free(h->d_ptf, synced);
+    dev_free(h->d_margf, synced);
+    dev_free(h->d_oh, synced);
+    dev_free(h->d_cmp, synced);
+    dev_free(h->d_firsts, synced);
+    dev_free(h->d_tiles, synced);
+    dev_free(h->d_cd, synced);
+    dev_free(h->d_prof, synced);
+    host_free(h->h_ctrl);
+    host_free(h->h_scores);
+    host_free(h->h_trip);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : h->cmp_ev) cudaEventDestroy(e);
@@ -367,17 +412,18 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     uint8_t* d_pheno = nullptr;
     int* d_counts = nullptr;
     int rc = EPI3_OK;
+    bool synced = false;   // the stream that used the temporaries has been synchronised
     auto cleanup = [&]() {
         if (!(h->flags & EPI3_DEVICE_PTRS)) {
-            dev_free(d_geno);
-            dev_free(d_pheno);
+            dev_free(d_geno, synced);
+            dev_free(d_pheno, synced);
         }
-        dev_free(d_counts);
+        dev_free(d_counts, synced);
     };
     do {
         cudaError_t e;
         if ((e = dev_alloc((void**)&h->d_ctrl, sizeof(Ctrl))) != cudaSuccess) { rc = cuda_fail(e, "alloc ctrl"); break; }
-        if ((e = cudaMallocHost((void**)&h->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { rc = cuda_fail(e, "pinned ctrl"); break; }
+        if ((e = host_alloc((void**)&h->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { rc = cuda_fail(e, "pinned ctrl"); break; }
         if (h->flags & EPI3_DEVICE_PTRS) {
             d_geno = const_cast<uint8_t*>(geno);
             d_pheno = const_cast<uint8_t*>(pheno);
@@ -391,10 +437,24 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
         if ((e = launch_reset(h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "reset"); break; }
         if ((e = launch_class_index(d_pheno, h->N, d_counts, h->d_ctrl, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index launch"); break; }
         int counts[2] = {0, 0};
-        if ((e = cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read counts"); break; }
-        if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
-        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index"); break; }
-        if (h->h_ctrl->status & kStBadPhenotype) { rc = fail(EPI3_ERR_ARG, "phenotype value > 1"); break; }
+        if (!(h->flags & EPI3_DEVICE_PTRS)) {
+            // host inputs: the class sizes come from the phenotype on the host, while the copies
+            // and the class index run (no wait for the device here)
+            int n1 = 0;
+            bool bad = false;
+            for (int t = 0; t < h->N; ++t) {
+                n1 += pheno[t] == 1;
+                bad |= pheno[t] > 1;
+            }
+            if (bad) { rc = fail(EPI3_ERR_ARG, "phenotype value > 1"); break; }
+            counts[0] = h->N - n1;
+            counts[1] = n1;
+        } else {
+            if ((e = cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read counts"); break; }
+            if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
+            if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "class_index"); break; }
+            if (h->h_ctrl->status & kStBadPhenotype) { rc = fail(EPI3_ERR_ARG, "phenotype value > 1"); break; }
+        }
         h->N0 = counts[0];
         h->N1 = counts[1];
         Planes& pl = h->pl;
@@ -413,7 +473,12 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
         if ((e = cudaEventRecord(h->ev[1], h->stream)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
         if ((e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) { rc = cuda_fail(e, "read status"); break; }
         if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(e, "pack"); break; }
-        if (h->h_ctrl->status & kStBadGenotype) { rc = fail(EPI3_ERR_ARG, "genotype value > 2"); break; }
+        synced = true;
+        if (h->h_ctrl->status & (kStBadGenotype | kStBadPhenotype)) {
+            rc = fail(EPI3_ERR_ARG, (h->h_ctrl->status & kStBadGenotype) ? "genotype value > 2"
+                                                                            : "phenotype value > 1");
+            break;
+        }
         cudaEventElapsedTime(&h->stats.pack_ms, h->ev[0], h->ev[1]);
     } while (0);
     cleanup();
@@ -428,8 +493,8 @@ int create_impl(epi3_handle* h, const uint8_t* geno, const uint8_t* pheno) {
     CK(dev_alloc((void**)&h->d_fin, sizeof(Final) * kFinalCap), "alloc final");
     CK(dev_alloc((void**)&h->d_out_scores, sizeof(double) * EPI3_MAX_TOPK), "alloc out scores");
     CK(dev_alloc((void**)&h->d_out_trip, sizeof(int) * 3 * EPI3_MAX_TOPK), "alloc out triplets");
-    CK(cudaMallocHost((void**)&h->h_scores, sizeof(double) * EPI3_MAX_TOPK), "pinned scores");
-    CK(cudaMallocHost((void**)&h->h_trip, sizeof(int) * 3 * EPI3_MAX_TOPK), "pinned triplets");
+    CK(host_alloc((void**)&h->h_scores, sizeof(double) * EPI3_MAX_TOPK), "pinned scores");
+    CK(host_alloc((void**)&h->h_trip, sizeof(int) * 3 * EPI3_MAX_TOPK), "pinned triplets");
     return EPI3_OK;
 }
 
@@ -439,8 +504,9 @@ int ensure_pair_tables(epi3_handle* h) {
     const long long np = pairs(h->M);
     CK(dev_alloc((void**)&h->d_pt, sizeof(int4) * 2 * (size_t)np), "alloc pair tables");
     CK(dev_alloc((void**)&h->d_marg, sizeof(int2) * 2 * (size_t)h->M), "alloc marginals");
+    // stream-ordered: every consumer runs on the handle's stream (the host reads the marginals
+    // after synchronising it)
     CK(launch_pair_tables(h->pl, h->d_pt, h->d_marg, np, h->stream), "pair tables launch");
-    CK(cudaStreamSynchronize(h->stream), "pair tables");
     h->ptab.pt = h->d_pt;
     h->ptab.marg = h->d_marg;
     h->ptab.n_pairs = np;
@@ -845,8 +911,9 @@ int cmp_prepare(epi3_handle* h, long long pb, long long pe, CmpPlan& P) {
     const int M = h->M;
     if (h->h_marg.empty()) {
         h->h_marg.resize(2 * (size_t)M);
-        CK(cudaMemcpy(h->h_marg.data(), h->d_marg, sizeof(int2) * 2 * (size_t)M,
-                      cudaMemcpyDeviceToHost), "read marginals");
+        CK(cudaMemcpyAsync(h->h_marg.data(), h->d_marg, sizeof(int2) * 2 * (size_t)M,
+                           cudaMemcpyDeviceToHost, h->stream), "read marginals");
+        CK(cudaStreamSynchronize(h->stream), "read marginals");
     }
     plan_cmp(h, pb, pe, P);
     dev_free(h->d_firsts);
@@ -1547,22 +1614,22 @@ namespace {
 
 void batch_release(epi3_batch* b) {
     if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
+    const bool synced = b->stream && cudaStreamSynchronize(b->stream) == cudaSuccess;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (epi3_handle* h : b->h) {
         if (!h) continue;
         h->d_ctrl = nullptr;  // owned by the batch
         release(h);
     }
-    dev_free(b->d_ctrls);
-    cudaFreeHost(b->h_ctrls);
-    dev_free(b->d_cds);
-    dev_free(b->d_tiles);
-    dev_free(b->d_cmp);
-    dev_free(b->d_scores);
-    dev_free(b->d_trip);
-    cudaFreeHost(b->h_scores);
-    cudaFreeHost(b->h_trip);
+    dev_free(b->d_ctrls, synced);
+    host_free(b->h_ctrls);
+    dev_free(b->d_cds, synced);
+    dev_free(b->d_tiles, synced);
+    dev_free(b->d_cmp, synced);
+    dev_free(b->d_scores, synced);
+    dev_free(b->d_trip, synced);
+    host_free(b->h_scores);
+    host_free(b->h_trip);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1943,7 +2010,7 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(e, "event create"));
     if ((e = dev_alloc((void**)&b->d_ctrls, sizeof(Ctrl) * n_cohorts)) != cudaSuccess)
         return bail(cuda_fail(e, "alloc control blocks"));
-    if ((e = cudaMallocHost((void**)&b->h_ctrls, sizeof(Ctrl) * n_cohorts)) != cudaSuccess)
+    if ((e = host_alloc((void**)&b->h_ctrls, sizeof(Ctrl) * n_cohorts)) != cudaSuccess)
         return bail(cuda_fail(e, "pinned control blocks"));
     b->h.assign(n_cohorts, nullptr);
     b->path.assign(n_cohorts, EPI3_PATH_POPC8);
@@ -2001,8 +2068,8 @@ int epi3_batch_create(epi3_batch** out, int32_t n_cohorts, const epi3_cohort* co
     const size_t nk = (size_t)n_cohorts * EPI3_MAX_TOPK;
     if ((e = dev_alloc((void**)&b->d_scores, sizeof(double) * nk)) != cudaSuccess ||
         (e = dev_alloc((void**)&b->d_trip, sizeof(int) * 3 * nk)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&b->h_scores, sizeof(double) * nk)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&b->h_trip, sizeof(int) * 3 * nk)) != cudaSuccess)
+        (e = host_alloc((void**)&b->h_scores, sizeof(double) * nk)) != cudaSuccess ||
+        (e = host_alloc((void**)&b->h_trip, sizeof(int) * 3 * nk)) != cudaSuccess)
         return bail(cuda_fail(e, "alloc batch outputs"));
     *out = b;
     return EPI3_OK;
