@@ -218,6 +218,44 @@ inline int cmp_drop(int n0, int n1, int n2) {
     if (n2 >= n0 && n2 >= n1) return 2;
     return n0 >= n1 ? 0 : 1;
 }
+// A first SNP whose derived genotype d is not 2 counts the other two: slot s = 0, 1 holds
+// genotype cmp_geno(d, s) and the derived genotype takes label 2 (in both classes alike), so the
+// tensor scan's inclusion-exclusion and bound run unchanged on relabelled inputs (every value an
+// exact integer; the bound is a sum over cells, each cell pairing its two classes).
+// Pair table (X = first SNP, W) of a class, n(a, w) at 2 a + w, with W's marginal {n0, n1}.
+__host__ __device__ __forceinline__ int4 relabel_xy(int4 p, int2 mw, int d) {
+    const int n20 = mw.x - p.x - p.z, n21 = mw.y - p.y - p.w;
+    return d == 0 ? make_int4(p.z, p.w, n20, n21) : d == 1 ? make_int4(p.x, p.y, n20, n21) : p;
+}
+// Marginal of the first SNP {n0, n1} in a class of nc samples.
+__host__ __device__ __forceinline__ int2 relabel_marg(int2 m, int nc, int d) {
+    const int n2 = nc - m.x - m.y;
+    return d == 0 ? make_int2(m.y, n2) : d == 1 ? make_int2(m.x, n2) : m;
+}
+// The same for the FP32 pair-table row (X, Z) (+ 3 each, index 2 a + z) with Z's marginal + 9
+// (exact: integers below 2^24).
+__host__ __device__ __forceinline__ float4 relabel_xz(float4 x, float2 mz9, int d) {
+    if (d == 2) return x;
+    const float r0 = (mz9.x - x.x) - x.z, r1 = (mz9.y - x.y) - x.w;
+    return d == 0 ? make_float4(x.z, x.w, r0, r1) : make_float4(x.x, x.y, r0, r1);
+}
+// Cells u[9 a + 3 b + z] of relabelled first-SNP genotypes back in genotype order.
+template <class T>
+__host__ __device__ __forceinline__ void canon_rows(T* u, int d) {
+    if (d == 2) return;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const T r0 = u[e], r1 = u[9 + e], r2 = u[18 + e];   // slot 0, slot 1, derived
+        if (d == 0) {            // genotypes 1, 2, 0
+            u[e] = r2;
+            u[9 + e] = r0;
+            u[18 + e] = r1;
+        } else {                 // genotypes 0, 2, 1
+            u[9 + e] = r2;
+            u[18 + e] = r1;
+        }
+    }
+}
 // compacted chunks of one first SNP: 16 KB each
 inline long long cmp_chunks_of(const CmpFirst& f, int M) {
     const long long nblk = (M + 63) / 64 - f.b_lo;

@@ -99,43 +99,6 @@ __device__ __forceinline__ void cmp_push(uint8_t* set_base, uint8_t* slab, int r
     }
 }
 
-// A first SNP whose derived genotype d is not 2 counts the other two: slot s = 0, 1 holds
-// genotype cmp_geno(d, s) and the derived genotype takes label 2 (in both classes alike), so
-// the epilogue's inclusion-exclusion and bound run unchanged on relabelled inputs (every value
-// an exact integer; the bound is a sum over cells, each cell pairing its two classes).
-// Pair table (X = first SNP, Y) of a class, n(a, b) at 2 a + b, with Y's marginal.
-__device__ __forceinline__ int4 relabel_xy(int4 p, int2 my, int d) {
-    const int n20 = my.x - p.x - p.z, n21 = my.y - p.y - p.w;
-    return d == 0 ? make_int4(p.z, p.w, n20, n21) : d == 1 ? make_int4(p.x, p.y, n20, n21) : p;
-}
-// Marginal of the first SNP (#0, #1) in a class of nc samples.
-__device__ __forceinline__ int2 relabel_marg(int2 m, int nc, int d) {
-    const int n2 = nc - m.x - m.y;
-    return d == 0 ? make_int2(m.y, n2) : d == 1 ? make_int2(m.x, n2) : m;
-}
-// FP32 pair-table row (X, Z) (+ 3 each, index 2 a + z) with Z's marginal + 9.
-__device__ __forceinline__ float4 relabel_xz(float4 x, float2 mz9, int d) {
-    if (d == 2) return x;
-    const float r0 = __fsub_rn(__fsub_rn(mz9.x, x.x), x.z), r1 = __fsub_rn(__fsub_rn(mz9.y, x.y), x.w);
-    return d == 0 ? make_float4(x.z, x.w, r0, r1) : make_float4(x.x, x.y, r0, r1);
-}
-// Cells u[9 a + 3 b + z] of relabelled first-SNP genotypes back in genotype order.
-__device__ __forceinline__ void canon_rows(float* u, int d) {
-    if (d == 2) return;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-        const float r0 = u[e], r1 = u[9 + e], r2 = u[18 + e];   // slot 0, slot 1, derived
-        if (d == 0) {            // genotypes 1, 2, 0
-            u[e] = r2;
-            u[9 + e] = r0;
-            u[18 + e] = r1;
-        } else {                 // genotypes 0, 2, 1
-            u[9 + e] = r2;
-            u[18 + e] = r1;
-        }
-    }
-}
-
 constexpr int kCompactThreads = 128;     // one row (SNP, genotype) of the 64-SNP block per thread
 
 // Push the bits of one 32-sample word selected by a set's mask: compress by the mask (Hacker's

@@ -1,6 +1,8 @@
 """Host-side checks of library code that needs no GPU (compiled as host code with nvcc): the
-exact 8 -> 27 cell derivation against brute-force counting, and the bit extraction of the
-sample compaction against a plain bit loop."""
+exact 8 -> 27 cell derivation against brute-force counting, the bit extraction of the sample
+compaction against a plain bit loop, and the compacted scan's derived first-SNP genotype
+(counted-genotype slots, relabelled pair tables and marginals, cell order restored) against
+brute-force tables."""
 import os
 import shutil
 import subprocess
@@ -30,3 +32,14 @@ def test_bit_compress_matches_bit_loop(tmp_path):
                            os.path.join(HERE, "host", "bit_compress_check.cu")])
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and "bit compress ok" in out.stdout, out.stdout + out.stderr
+
+
+def test_derived_genotype_relabelling_matches_bruteforce(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "relabel_check"
+    subprocess.check_call([nvcc, "-std=c++17", "-o", str(exe),
+                           os.path.join(HERE, "host", "relabel_check.cu")])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and "relabel ok" in out.stdout, out.stdout + out.stderr
