@@ -931,7 +931,6 @@ int scan_cmp_impl(epi3_handle* h, long long pb, long long pe, long long nt, int 
     CmpPlan P;
     const int prc = cmp_prepare(h, pb, pe, P);
     if (prc != EPI3_OK) return prc;
-    const std::vector<CmpFirst>& firsts = P.firsts;
     const std::vector<int>& range_start = P.range_start;
     const std::vector<long long>& range_tiles = P.range_tiles;
     const int i_hi = P.i_hi;
