@@ -15,10 +15,11 @@ oracle's own code path as its expected value:
   Sec. III);
 * pairs (Eq. 1 for two SNPs, 9 cells): numpy bincount, big-integer K2, and the
   triplet K2 of a monomorphic third SNP, which must equal the pair K2 exactly;
-* any order (Eq. 1 for k SNPs, 3^k cells): numpy bincount of the base-3 cell,
+* any order (Eq. 1 for k SNPs, 3^k cells, k up to 6): numpy bincount of the base-3 cell,
   big-integer K2, summing out a SNP gives the lower-order table, orders 2 and 3
-  equal the pair and triplet functions bit for bit, a monomorphic fourth SNP
-  gives the triplet K2 exactly, and numpy lexsort over every 4-SNP set.
+  equal the pair and triplet functions bit for bit, a monomorphic last SNP
+  gives the lower-order K2 exactly (orders 4, 5, 6), and numpy lexsort over every
+  4-, 5- and 6-SNP set of small cases.
 """
 from __future__ import annotations
 
@@ -323,7 +324,8 @@ def exact_k2_cells(table):
 
 def check_order_tables_bruteforce(o):
     for (m, n, n1, seed, order) in [(7, 61, 25, 51, 4), (6, 130, 129, 52, 4), (6, 40, 17, 53, 5),
-                                    (5, 33, 10, 54, 1), (6, 97, 40, 55, 3)]:
+                                    (5, 33, 10, 54, 1), (6, 97, 40, 55, 3), (8, 77, 30, 65, 6),
+                                    (7, 200, 199, 66, 5)]:
         g, ph = tiny_data(m, n, n1, seed)
         sets = all_sets(m, order)
         want = numpy_order_tables(g, ph, sets)
@@ -391,6 +393,38 @@ def check_order_scan_bruteforce(o):
         assert np.array_equal(sc, s_oracle[rank[:k]])
 
 
+def check_order5_6_scan_bruteforce(o):
+    # orders 5 and 6: big-integer K2 of every set, ranked by (K2, indices), against the scan
+    for (m, n, n1, seed, order, k) in [(8, 90, 41, 67, 5, 20), (7, 60, 31, 68, 5, 21),
+                                       (8, 130, 64, 69, 6, 28), (7, 45, 0, 70, 6, 7)]:
+        g, ph = tiny_data(m, n, n1, seed)
+        sets = all_sets(m, order)
+        s = np.array([exact_k2_cells(t) for t in numpy_order_tables(g, ph, sets)])
+        s_oracle = o.k2_cells(o.tables_order(g, ph, sets))
+        assert np.allclose(s_oracle, s, rtol=1e-13)
+        rank = np.lexsort(tuple(sets[:, t] for t in range(order - 1, -1, -1)) + (s_oracle,))
+        x, sc, _ = o.scan_order_topk(g, ph, order, k)
+        assert np.array_equal(x, sets[rank[:k]])
+        assert np.array_equal(sc, s_oracle[rank[:k]])
+
+
+def check_order5_6_marginals_and_monomorphic(o):
+    # summing an order-5 (order-6) table over the last SNP's digit gives the order-4 (order-5)
+    # table of the other SNPs; a monomorphic last SNP leaves the lower-order K2 bit for bit
+    g, ph = tiny_data(9, 140, 60, 71)
+    for order in (5, 6):
+        sets = all_sets(8, order)
+        t = o.tables_order(g, ph, sets).reshape((len(sets), 2) + (3,) * order)
+        low = o.tables_order(g, ph, np.ascontiguousarray(sets[:, :order - 1]))
+        assert np.array_equal(t.sum(axis=order + 1).reshape(len(sets), 2, -1), low)
+    g[8] = 0
+    for order in (5, 6):
+        lower = all_sets(8, order - 1)
+        sets = np.concatenate([lower, np.full((len(lower), 1), 8, dtype=np.int32)], axis=1)
+        assert np.array_equal(o.k2_cells(o.tables_order(g, ph, sets)),
+                              o.k2_cells(o.tables_order(g, ph, lower)))
+
+
 def check_order_ties(o):
     # a duplicated SNP column gives 4-SNP sets with identical tables: equal K2, ordered by
     # their indices
@@ -412,4 +446,5 @@ ALL_CHECKS = [check_lf, check_hand_values, check_k2_bigint, check_tables_brutefo
               check_pair_tables_bruteforce, check_pair_scan_bruteforce, check_pair_vs_triplet,
               check_pair_ties_and_degenerate, check_order_tables_bruteforce, check_order_k2_bigint,
               check_order_marginals, check_order_matches_lower_orders, check_order_monomorphic,
-              check_order_scan_bruteforce, check_order_ties]
+              check_order_scan_bruteforce, check_order5_6_scan_bruteforce,
+              check_order5_6_marginals_and_monomorphic, check_order_ties]
